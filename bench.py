@@ -1,0 +1,406 @@
+"""Throughput benchmark of the MBBP-LD hot path on GB300.
+
+Workload (one "step"): the [[144,12,12]] bivariate bicycle code under
+code-capacity depolarizing noise at p in {0.02, 0.04, 0.06, 0.08}; for every p,
+SHOTS fresh shots are sampled on the GPU, the X part is decoded with the R=16
+representations of H_Z and the Z part with those of H_X (100 iterations,
+normalized min-sum, alpha = 0.625, FP32), FWS selects, and the logical judge
+counts failures.  Every stage runs in the library's kernels through the C ABI.
+
+Output: one JSON line (rank 0).  ``value`` = depolarizing shots per second
+(both error types decoded) with everything resident in HBM; ``e2e`` = the same
+metric through mbbp_decode with pinned host syndromes copied in and estimates
+copied out inside the timed region.  ``--impl reference`` times the CPU
+oracle instead (the slow plain restatement of the method), on a bounded
+sample of the same workload.
+
+Multi-GPU (torchrun): rank r decodes its own shot range each step; the only
+exchange is the failure / work counters, summed once after timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CODE = "bb144"
+P_LIST = (0.02, 0.04, 0.06, 0.08)
+R = 16
+ITERS = 100
+ALPHA = 0.625
+SEED = 20260515
+OPS_PER_EDGE_UPDATE = 10  # algorithmic ALU operations per edge-update (min-sum flooding)
+WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shots", type=int, default=1_000_000, help="shots per p per step per GPU")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        loaded = [c for c, _, _ in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(m for _, m, _ in rows),
+                "reasons": seen, "samples": len(rows)}
+
+
+def cpu_baseline(seconds: float):
+    """The oracle (FP64, as it stands) on host cores: shots/s of the same
+    workload on a bounded sample (shots taken round-robin over p)."""
+    import concurrent.futures as cf
+
+    import oracle
+    from paper_2605_14170_gb300.inputs import named_code
+
+    code = named_code(CODE)
+    n = code.n
+    cores = os.cpu_count() or 1
+    sets = {"HZ": oracle.collect_subtrees(code.HZ, R, SEED), "HX": oracle.collect_subtrees(code.HX, R, SEED + 1)}
+    chunk = 4
+
+    def work(k):
+        p = P_LIST[k % len(P_LIST)]
+        first = 10_000_000 + chunk * k
+        ex, ez = oracle.sample(SEED, first, chunk, n, p, "depolarizing")
+        pm = 2 * p / 3
+        llr = np.full(n, np.log((1 - pm) / pm))
+        for H, e, key in ((code.HZ, ex, "HZ"), (code.HX, ez, "HX")):
+            s = oracle.syndrome(H, e)
+            oracle.mbbp_decode(H, sets[key], s, llr, ITERS, ALPHA, precision="f64")
+        return chunk
+
+    done = 0
+    t0 = time.perf_counter()
+    k = 0
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        futs = set()
+        while time.perf_counter() - t0 < seconds or futs:
+            while len(futs) < cores and time.perf_counter() - t0 < seconds:
+                futs.add(ex.submit(work, k))
+                k += 1
+            finished, futs = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            done += sum(f.result() for f in finished)
+    dt = time.perf_counter() - t0
+    # every chunk covers one p; the workload mixes the four p equally, which the
+    # round-robin order reproduces up to the last partial round
+    return {"value": done / dt, "unit": "shots/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} depolarizing shots of the workload (X and Z decoded, p round-robin over "
+                      f"{list(P_LIST)}), oracle FP64, {cores} threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    budget = max(2.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        cpu_baseline(budget / 4)
+    vals, t_all = [], time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(budget)["value"])
+    total = time.perf_counter() - t_all
+    value = statistics.mean(vals)
+    cb = cpu_baseline(budget)
+    line = {
+        "impl": "reference", "metric": "decoded shots/s", "value": value, "unit": "shots/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shots_per_p": args.shots},
+        "cpu_baseline": {"value": value, "unit": "shots/s", "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2605_14170_gb300 import mbbp
+    from paper_2605_14170_gb300.inputs import named_code
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    code = named_code(CODE)
+    n = code.n
+    W = (n + 31) // 32
+    S = args.shots
+    BZ = mbbp.mbbp_build_bases(code.HZ, R, SEED)       # X errors
+    BX = mbbp.mbbp_build_bases(code.HX, R, SEED + 1)   # Z errors
+    LZ = mbbp.mbbp_logicals_build(code.HZ, code.HX)
+    LX = mbbp.mbbp_logicals_build(code.HX, code.HZ)
+    m = code.HZ.shape[0]
+    llrs = {p: torch.full((n,), float(np.log((1 - 2 * p / 3) / (2 * p / 3))), dtype=torch.float32, device=dev)
+            for p in P_LIST}
+    edges = {"Z": torch.from_numpy(BZ.edges.astype(np.int64)).to(dev),
+             "X": torch.from_numpy(BX.edges.astype(np.int64)).to(dev)}
+
+    ex = torch.empty((S, W), dtype=torch.int32, device=dev)
+    ez = torch.empty((S, W), dtype=torch.int32, device=dev)
+    syn = torch.empty((S, m), dtype=torch.uint8, device=dev)
+    ws = torch.empty(mbbp.mbbp_decode_workspace_size(BZ, S), dtype=torch.uint8, device=dev)
+    e_hat = torch.empty((S, n), dtype=torch.uint8, device=dev)
+    conv = torch.empty((S, R), dtype=torch.uint8, device=dev)
+    iters = torch.empty((S, R), dtype=torch.int16, device=dev)
+    succ = torch.empty((S,), dtype=torch.uint8, device=dev)
+    fail_x = torch.empty((S,), dtype=torch.uint8, device=dev)
+    fail_z = torch.empty((S,), dtype=torch.uint8, device=dev)
+    counts = torch.zeros((len(P_LIST), 3, 3), dtype=torch.int64, device=dev)  # p, type(X,Z,any), code
+    work = torch.zeros((), dtype=torch.int64, device=dev)
+    dec_events = []
+    launches_per_step = 0
+
+    def step(k, record=False):
+        nonlocal launches_per_step
+        launches = 0
+        for ip, p in enumerate(P_LIST):
+            first = ((k * world + rank) * len(P_LIST) + ip) * S
+            mbbp.mbbp_sample_errors(n, S, first, SEED, p, mbbp.NOISE_DEPOLARIZING, ex, ez)
+            launches += 1
+            for key, B, L, e, fl in (("Z", BZ, LZ, ex, fail_x), ("X", BX, LX, ez, fail_z)):
+                mbbp.mbbp_syndrome(B, e, syn)
+                if record:
+                    ev0 = torch.cuda.Event(enable_timing=True)
+                    ev1 = torch.cuda.Event(enable_timing=True)
+                    ev0.record(stream)
+                mbbp.mbbp_decode(B, syn, llrs[p], ITERS, ALPHA, mbbp.RULE_NMS, e_hat, conv, succ, ws,
+                                 iters_run=iters)
+                if record:
+                    ev1.record(stream)
+                    dec_events.append((ev0, ev1, key))
+                mbbp.mbbp_judge(L, e, e_hat, fl, counts[ip, 0 if key == "Z" else 1])
+                launches += 4  # syndrome, BP, FWS, judge
+                work.add_((iters.to(torch.int64) & 0xFFFF).sum(0) @ edges[key])
+            # any-type failure for the combined logical error rate
+            counts[ip, 2, 1] += ((fail_x != 0) | (fail_z != 0)).sum()
+        launches_per_step = launches
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    counts.zero_()
+    work.zero_()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            step(args.warmup + k, record=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(counts)
+        dist.all_reduce(work)
+    ms = float(ms_t.item())
+    shots_total = args.steps * len(P_LIST) * S * world
+    value = shots_total / (ms / 1000.0)
+    edge_updates = int(work.item())
+    dec_ms = [a.elapsed_time(b) for a, b, _ in dec_events]
+    dec_avg_ms = statistics.mean(dec_ms)
+    # per-launch algorithmic work of the decode call
+    edge_per_launch = edge_updates / max(len(dec_ms) * world, 1)
+    peaks, peak_kind = read_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    peak_ops = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    achieved_ops = OPS_PER_EDGE_UPDATE * edge_per_launch / (dec_avg_ms / 1000.0)
+    cnt = counts.cpu().numpy()
+    ler = {str(p): {"x": float(cnt[i, 0, 2] + cnt[i, 0, 1]) / (args.steps * S * world),
+                    "z": float(cnt[i, 1, 2] + cnt[i, 1, 1]) / (args.steps * S * world),
+                    "any": float(cnt[i, 2, 1]) / (args.steps * S * world)} for i, p in enumerate(P_LIST)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, mbbp, BZ, BX, llrs, S, dev, stream, rank, world)
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "decoded shots/s", "value": value, "unit": "shots/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "code": "[[144,12,12]]", "R": R, "iters": ITERS,
+                       "alpha": ALPHA, "rule": "normalized min-sum, flooding", "p": list(P_LIST),
+                       "shots_per_p_per_gpu": S, "noise": "code-capacity depolarizing",
+                       "l2": "inputs larger than L2 (per decode call: "
+                             f"{S * m / 1e6:.0f} MB syndromes, {ws.numel() / 1e6:.0f} MB workspace, "
+                             f"{S * n / 1e6:.0f} MB estimates)"},
+            "edge_updates_per_s": edge_updates / (ms / 1000.0),
+            "decoded_syndromes_per_s": 2 * value,
+            "ler": ler,
+            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                         "kernel": "mbbp_decode (BP + FWS)", "decode_ms_avg": dec_avg_ms,
+                         "edge_updates_per_launch": edge_per_launch,
+                         "ops_per_edge_update": OPS_PER_EDGE_UPDATE,
+                         "peak_basis": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                       f"({peak_kind} max SM clock)"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+        }
+        if e2e is not None:
+            line["e2e"] = e2e
+        if cb is not None:
+            line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, mbbp, BZ, BX, llrs, S, dev, stream, rank, world):
+    """Same metric through mbbp_decode with host buffers: pinned syndromes in,
+    estimates / flags / success out, inside the timed region."""
+    import torch
+    n, m = BZ.n, BZ.m
+    W = (n + 31) // 32
+    # host syndromes prepared before timing (GPU sampler + syndrome, copied out)
+    ex = torch.empty((S, W), dtype=torch.int32, device=dev)
+    ez = torch.empty((S, W), dtype=torch.int32, device=dev)
+    syn_d = torch.empty((S, m), dtype=torch.uint8, device=dev)
+    host_s = {}
+    for ip, p in enumerate(P_LIST):
+        mbbp.mbbp_sample_errors(n, S, (world * 1000 + rank * len(P_LIST) + ip) * S, SEED + 7, p,
+                                mbbp.NOISE_DEPOLARIZING, ex, ez)
+        for key, B, e in (("Z", BZ, ex), ("X", BX, ez)):
+            mbbp.mbbp_syndrome(B, e, syn_d)
+            h = torch.empty((S, m), dtype=torch.uint8, pin_memory=True)
+            h.copy_(syn_d)
+            host_s[(p, key)] = h
+    torch.cuda.synchronize()
+    out_h = {k: torch.empty((S, n), dtype=torch.uint8, pin_memory=True) for k in ("Z", "X")}
+    conv_h = {k: torch.empty((S, BZ.R), dtype=torch.uint8, pin_memory=True) for k in ("Z", "X")}
+    succ_h = {k: torch.empty((S,), dtype=torch.uint8, pin_memory=True) for k in ("Z", "X")}
+    ws = torch.empty(mbbp.mbbp_decode_workspace_size(BZ, S), dtype=torch.uint8, device=dev)
+    e_hat = torch.empty((S, n), dtype=torch.uint8, device=dev)
+    conv = torch.empty((S, BZ.R), dtype=torch.uint8, device=dev)
+    succ = torch.empty((S,), dtype=torch.uint8, device=dev)
+
+    def step():
+        for p in P_LIST:
+            for key, B in (("Z", BZ), ("X", BX)):
+                syn_d.copy_(host_s[(p, key)], non_blocking=True)
+                mbbp.mbbp_decode(B, syn_d, llrs[p], ITERS, ALPHA, mbbp.RULE_NMS, e_hat, conv, succ, ws)
+                out_h[key].copy_(e_hat, non_blocking=True)
+                conv_h[key].copy_(conv, non_blocking=True)
+                succ_h[key].copy_(succ, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dt], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    shots = args.steps * len(P_LIST) * S * world
+    return {"value": shots / dt, "unit": "shots/s",
+            "h2d_bytes_per_step": len(P_LIST) * 2 * S * m,
+            "d2h_bytes_per_step": len(P_LIST) * 2 * S * (n + BZ.R + 1)}
+
+
+if __name__ == "__main__":
+    main()

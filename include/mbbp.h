@@ -1,0 +1,225 @@
+/* mbbp.h — C ABI of the GB300 (sm_103a) Multiple-Bases BP List Decoder.
+ *
+ * The decoder of "Multiple-Bases Belief Propagation List Decoding for
+ * Quantum LDPC Codes" (Rabeti & Mahdavifar): syndrome-based belief
+ * propagation run in parallel over R redundant parity-check representations
+ * H^(t) = [H; H_t] (Section III-A, Eq. (4)) built from the maximal subtrees of
+ * Algorithm 2, followed by Frequency-Weighted Scoring of the converged
+ * candidates (Section III-B).  Algorithm 1 states the whole decoder.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major.  A "host" pointer is ordinary CPU memory, a
+ *    "device" pointer is CUDA global memory of the current device.
+ *  - Bit vectors are packed little-endian into uint32_t words: bit i of word
+ *    w is entry 32*w + i; W(n) = ceil(n / 32) words per vector; bits past n
+ *    are zero on output and ignored on input.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Entry points that take a stream only enqueue work on it and
+ *    return before it runs; they allocate no memory.
+ *  - Errors are status codes; nothing throws across the ABI and no kernel
+ *    traps.  mbbp_last_error() gives a message for the last non-OK status of
+ *    the calling thread.
+ *  - Handles (mbbp_bases, mbbp_logicals) are owned by the library and freed
+ *    with their *_free function; they hold host and device copies of their
+ *    tables and belong to the device that was current when they were built.
+ */
+#ifndef MBBP_H
+#define MBBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MBBP_OK = 0,
+    MBBP_E_INVALID = 1,   /* an argument is out of range or inconsistent      */
+    MBBP_E_TOO_LARGE = 2, /* sizes beyond the limits below                    */
+    MBBP_E_CUDA = 3,      /* a CUDA runtime call failed                       */
+    MBBP_E_TIMEOUT = 4,   /* a bounded device-side wait gave up               */
+    MBBP_E_NOMEM = 5,     /* host or device allocation failed                 */
+    MBBP_E_NOT_FOUND = 6  /* fewer distinct subtrees than requested exist     */
+} mbbp_status;
+
+/* Check-node rules (Section II-B). */
+enum { MBBP_RULE_NMS = 0, /* normalized min-sum, Eq. (2)                       */
+       MBBP_RULE_SP = 1   /* sum-product: 2 atanh(prod tanh(q/2)), used by the
+                             BPGD baselines of Section IV                      */ };
+
+/* Noise models of the error sampler. */
+enum { MBBP_NOISE_BSC = 0,          /* independent X errors (Section IV)     */
+       MBBP_NOISE_DEPOLARIZING = 1  /* X, Y, Z each with probability p/3     */ };
+
+/* Limits. */
+#define MBBP_MAX_R 64          /* representations per handle                   */
+#define MBBP_MAX_N 16384       /* variables (qubits)                           */
+#define MBBP_MAX_ROW_WEIGHT 12 /* check degree d_c of H                        */
+#define MBBP_MAX_COL_WEIGHT 12 /* variable degree in any H^(t)                 */
+#define MBBP_MAX_SLOTS 65536   /* d_c * (rows of the largest H^(t), padded to 32) */
+#define MBBP_MAX_ITERS 65535
+
+/* Readings of the paper that the kernels fix (the paper states none):
+ * v->c messages are clamped to [-MBBP_LMAX, MBBP_LMAX]; the min of Eq. (2)
+ * also runs over MBBP_LMAX (a degree-1 row sends alpha*LMAX); sum-product
+ * products are clamped to [-MBBP_PMAX, MBBP_PMAX] before atanh. */
+#define MBBP_LMAX 1.0e4f
+#define MBBP_PMAX (1.0f - 1.0f / 8388608.0f)
+
+typedef struct mbbp_bases mbbp_bases;
+typedef struct mbbp_logicals mbbp_logicals;
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char* mbbp_last_error(void);
+/* Library version string. */
+const char* mbbp_version(void);
+
+/* ------------------------------------------------------------------------
+ * Representation construction (host only, Section III-A).
+ * ---------------------------------------------------------------------- */
+
+/* Root order pi_j for Algorithm 2 (Section III-A: "different permutations
+ * lead to different collections").  pi_0 is the identity; for j >= 1 the
+ * identity is shuffled by Fisher-Yates (i = m-1 down to 1, swap i with
+ * x mod (i+1)) with x the successive outputs of splitmix64 seeded with
+ * seed XOR j.  perm: host int32[m], written. */
+mbbp_status mbbp_permutation(uint64_t seed, int j, int m, int32_t* perm);
+
+/* Algorithm 2: partition the checks of H into maximal subtrees.
+ * H: host uint8[m*n] 0/1; perm: host int32[m], a permutation of 0..m-1 (root
+ * order).  check_sets: host int32[m], receives the 1-based subtree index of
+ * each check.  order: host int32[m] or NULL, receives the checks in the order
+ * they were accepted (subtree by subtree; BFS order inside each), which is
+ * the row order of H_t (Fig. 2).  n_subtrees: host int32, or NULL.
+ * Neighbours are visited in ascending index order; a check is tested at most
+ * once per subtree. */
+mbbp_status mbbp_subtrees(const uint8_t* H, int m, int n, const int32_t* perm,
+                          int32_t* check_sets, int32_t* order, int32_t* n_subtrees);
+
+/* The R subtrees used as representations: the subtrees of pi_0, pi_1, ... in
+ * creation order, skipping any whose check set equals an earlier one, until R
+ * are found (at most 1024 orders are tried; fewer found -> MBBP_E_NOT_FOUND).
+ * set_ptr: host int32[R+1]; set_rows: host int32[R*m]; subtree t has rows
+ * set_rows[set_ptr[t] .. set_ptr[t+1]) in acceptance order. */
+mbbp_status mbbp_collect_subtrees(const uint8_t* H, int m, int n, int R, uint64_t seed,
+                                  int32_t* set_ptr, int32_t* set_rows);
+
+/* Build the R representations H^(t) = [H; H_t] (Eq. (4)) from the subtrees
+ * that mbbp_collect_subtrees(H, m, n, R, seed) returns, pack their Tanner
+ * graphs into the kernels' layout and copy them to the current device (a
+ * synchronous copy; call once per code).  H: host uint8[m*n] 0/1.  *out
+ * receives a handle owned by the library. */
+mbbp_status mbbp_build_bases(const uint8_t* H, int m, int n, int R, uint64_t seed,
+                             mbbp_bases** out);
+
+/* Same, with the extra rows of every representation given explicitly:
+ * representation t appends rows set_rows[set_ptr[t] .. set_ptr[t+1]) of H, in
+ * that order (an empty set gives plain BP on H; any rows of H are allowed,
+ * e.g. the random augmentations the paper compares against in Table II). */
+mbbp_status mbbp_build_bases_from_sets(const uint8_t* H, int m, int n, int R,
+                                       const int32_t* set_ptr, const int32_t* set_rows,
+                                       mbbp_bases** out);
+
+/* Shape of a handle.  Each output is host memory or NULL: m, n, R (int32);
+ * rows, edges (int32[R]: rows and edges of each H^(t)); set_ptr (int32[R+1])
+ * and set_rows (int32[set_ptr[R]]): the extra rows. */
+mbbp_status mbbp_bases_info(const mbbp_bases* B, int32_t* m, int32_t* n, int32_t* R,
+                            int32_t* rows, int32_t* edges, int32_t* set_ptr,
+                            int32_t* set_rows);
+
+/* Free a handle and its device tables (NULL is a no-op).  Not stream-ordered:
+ * no work that uses B may still be pending. */
+void mbbp_bases_free(mbbp_bases* B);
+
+/* ------------------------------------------------------------------------
+ * Monte-Carlo producer (Section IV: independent X errors; code-capacity
+ * depolarizing noise for the other workloads).
+ * ---------------------------------------------------------------------- */
+
+/* Sample errors for shots first_shot .. first_shot+batch-1 on n qubits.
+ * Qubit q of shot k draws u = output number k*n + q + 1 of splitmix64 seeded
+ * with `seed` (so any split of the shots gives the same errors);
+ * T = floor(p * 2^64), 0 <= p < 1.  BSC: X iff u < T.  Depolarizing, with
+ * t1 = floor(T/3): X iff u < t1, Y iff t1 <= u < 2 t1, Z iff 2 t1 <= u < T.
+ * ex: device uint32[batch*W(n)], X part (X or Y; decoded with H_Z).
+ * ez: device uint32[batch*W(n)] or NULL, Z part (Z or Y; decoded with H_X). */
+mbbp_status mbbp_sample_errors(int n, int batch, uint64_t first_shot, uint64_t seed,
+                               double p, int noise, uint32_t* ex, uint32_t* ez,
+                               void* stream);
+
+/* Syndromes s = H e over GF(2) for the H of a handle.  e: device
+ * uint32[batch*W(n)]; s: device uint8[batch*m], 0/1. */
+mbbp_status mbbp_syndrome(const mbbp_bases* B, int batch, const uint32_t* e, uint8_t* s,
+                          void* stream);
+
+/* ------------------------------------------------------------------------
+ * Decoder (Algorithm 1 with BP of Section II-B and FWS of Section III-B).
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace mbbp_decode needs for `batch` shots. */
+size_t mbbp_decode_workspace_size(const mbbp_bases* B, int batch);
+
+/* Decode `batch` syndromes on all R representations of B, then select.
+ *
+ * syndromes: device uint8[batch*m], 0/1 (bit r = check r of H).
+ * llr: device float[n] when llr_stride == 0 (one channel for every shot), or
+ *      float[batch*llr_stride] with llr_stride >= n (per-shot LLRs; the LLR
+ *      mu_i = log((1-p)/p) of Section II-B for an i.i.d. channel).
+ * iters: maximum BP iterations (0..MBBP_MAX_ITERS); alpha: normalization of
+ *      Eq. (2), 0 < alpha <= 1 (ignored by MBBP_RULE_SP); rule: MBBP_RULE_*.
+ * Every representation runs flooding BP: each iteration computes all check
+ * messages from the previous variable messages, then all variable messages,
+ * posteriors and hard decisions e_i = [m_i < 0].  It stops at the first
+ * iteration K (K = 0 is the hard decision of the LLRs themselves) whose hard
+ * decision satisfies H e = s, else after `iters`.  FWS picks, among the
+ * converged representations, the estimate maximising count / (weight + 1)
+ * (ties: lowest representation index); none converged -> e_hat = 0.
+ *
+ * Outputs (device): e_hat uint8[batch*n] 0/1; conv uint8[batch*R] (1 iff
+ * representation t converged); success uint8[batch] (1 iff any converged).
+ * Optional (device, or NULL): iters_run uint16[batch*R] (K of each
+ * representation); selected int16[batch] (chosen representation or -1);
+ * posterior float[batch*R*n] (last posterior LLRs of each representation).
+ * workspace: device memory of workspace_bytes >= mbbp_decode_workspace_size;
+ * on return (once the stream has run) its first batch*R*W(n) uint32 words
+ * hold the final hard decision of every (shot, representation), bit-packed,
+ * shot-major.  The call allocates nothing; concurrent calls need distinct
+ * workspaces. */
+mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                        const float* llr, int llr_stride, int iters, float alpha, int rule,
+                        uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run,
+                        uint8_t* success, int16_t* selected, float* posterior,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Logical-error judge (the logical error rate of Section IV).
+ * ---------------------------------------------------------------------- */
+
+/* Logical operators for judging errors decoded with H (m x n): a basis of
+ * ker(H_other) modulo rowspace(H), k = n - rank(H) - rank(H_other) vectors
+ * (for X errors: H = H_Z, H_other = H_X).  Host inputs; the handle keeps
+ * device copies. */
+mbbp_status mbbp_logicals_build(const uint8_t* H, int m, const uint8_t* H_other, int m_other,
+                                int n, mbbp_logicals** out);
+
+/* k and, if ops != NULL, the operators as host uint8[k*n]. */
+mbbp_status mbbp_logicals_info(const mbbp_logicals* L, int32_t* k, uint8_t* ops);
+
+/* Judge shots: r = e XOR e_hat; fail = 1 if H r != 0, 2 if H r = 0 but some
+ * logical operator has odd overlap with r, else 0.  e: device
+ * uint32[batch*W(n)]; e_hat: device uint8[batch*n]; fail: device uint8[batch]
+ * or NULL; counts: device uint64[3] or NULL, incremented by the number of
+ * shots with fail = 0, 1, 2 (zero it first to count one batch). */
+mbbp_status mbbp_judge(const mbbp_logicals* L, int batch, const uint32_t* e,
+                       const uint8_t* e_hat, uint8_t* fail, unsigned long long* counts,
+                       void* stream);
+
+/* Free a logicals handle (NULL is a no-op). */
+void mbbp_logicals_free(mbbp_logicals* L);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBBP_H */

@@ -1,0 +1,592 @@
+// Host side of the C ABI in include/mbbp.h: Algorithm 2 and the collection of
+// representations (Section III-A), packing of every H^(t) = [H; H_t]
+// (Eq. (4)) into the kernels' layout, the logical basis for the judge, and
+// argument checking for the launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "mbbp_internal.h"
+
+using namespace mbbp;
+
+struct mbbp_bases {
+    int m = 0, n = 0, R = 0, K = 0, DV = 0, MP = 0, mpad = 0, W = 0, regular = 0;
+    int device = 0, sm_count = 0;
+    std::vector<uint8_t> H;
+    std::vector<int32_t> set_ptr, set_rows, rows, edges;
+    void* dmem = nullptr;
+    DevBases dev{};
+};
+
+struct mbbp_logicals {
+    int m = 0, n = 0, k = 0, K = 0, mpad = 0, W = 0, device = 0;
+    std::vector<uint8_t> ops;  // k x n
+    void* dmem = nullptr;
+    DevLogicals dev{};
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+mbbp_status fail(mbbp_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+mbbp_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(MBBP_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// splitmix64 (Steele, Lea & Flood, OOPSLA 2014): output number i >= 1 of the
+// generator whose state starts at `state`.
+uint64_t sm64_at(uint64_t state, uint64_t i) {
+    uint64_t z = state + i * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+struct Tanner {
+    int m = 0, n = 0;
+    std::vector<std::vector<int>> rcols;  // columns of each row, ascending
+    std::vector<std::vector<int>> crows;  // rows of each column, ascending
+};
+
+mbbp_status make_tanner(const uint8_t* H, int m, int n, Tanner& g) {
+    if (!H) return fail(MBBP_E_INVALID, "H is NULL");
+    if (m < 1 || n < 1) return fail(MBBP_E_INVALID, "m and n must be >= 1");
+    if (m > 65535 || n > MBBP_MAX_N) return fail(MBBP_E_TOO_LARGE, "H is larger than the limits");
+    g.m = m;
+    g.n = n;
+    g.rcols.assign(m, {});
+    g.crows.assign(n, {});
+    for (int r = 0; r < m; ++r)
+        for (int v = 0; v < n; ++v) {
+            const uint8_t x = H[(size_t)r * n + v];
+            if (x > 1) return fail(MBBP_E_INVALID, "H entries must be 0 or 1");
+            if (x) {
+                g.rcols[r].push_back(v);
+                g.crows[v].push_back(r);
+            }
+        }
+    return MBBP_OK;
+}
+
+// Algorithm 2 on an adjacency-list Tanner graph.  Per-subtree "visited" and
+// "tested" marks are stamps equal to the current subtree index.
+int subtrees_impl(const Tanner& g, const int32_t* perm, int32_t* cs, int32_t* order) {
+    std::vector<int> vmark(g.n, 0), tmark(g.m, 0);
+    std::vector<int> queue;
+    std::fill(cs, cs + g.m, 0);
+    int s = 0, nord = 0;
+    for (int idx = 0; idx < g.m; ++idx) {
+        const int root = perm[idx];
+        if (cs[root] != 0) continue;
+        ++s;
+        queue.clear();
+        queue.push_back(root);
+        for (size_t head = 0; head < queue.size(); ++head) {
+            const int u = queue[head];
+            if (tmark[u] == s) continue;
+            tmark[u] = s;
+            int eta = 0;
+            for (int v : g.rcols[u]) eta += (vmark[v] == s) ? 1 : 0;
+            if (eta > 1) continue;
+            cs[u] = s;
+            if (order) order[nord++] = u;
+            for (int v : g.rcols[u]) {
+                vmark[v] = s;
+                for (int c : g.crows[v])
+                    if (tmark[c] != s && cs[c] == 0) queue.push_back(c);
+            }
+        }
+    }
+    return s;
+}
+
+void permutation_impl(uint64_t seed, int j, int m, int32_t* perm) {
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    if (j == 0) return;
+    const uint64_t state = seed ^ (uint64_t)j;
+    uint64_t draw = 0;
+    for (int i = m - 1; i >= 1; --i) {
+        const uint64_t x = sm64_at(state, ++draw);
+        std::swap(perm[i], perm[(int)(x % (uint64_t)(i + 1))]);
+    }
+}
+
+constexpr int kMaxPerms = 1024;
+
+mbbp_status collect_impl(const Tanner& g, int R, uint64_t seed, std::vector<int32_t>& set_ptr,
+                         std::vector<int32_t>& set_rows) {
+    std::vector<int32_t> perm(g.m), cs(g.m), order(g.m);
+    std::set<std::vector<int32_t>> seen;
+    set_ptr.assign(1, 0);
+    set_rows.clear();
+    int found = 0;
+    for (int j = 0; j < kMaxPerms && found < R; ++j) {
+        permutation_impl(seed, j, g.m, perm.data());
+        subtrees_impl(g, perm.data(), cs.data(), order.data());
+        int pos = 0;
+        while (pos < g.m && found < R) {
+            const int start = pos, t = cs[order[pos]];
+            while (pos < g.m && cs[order[pos]] == t) ++pos;
+            std::vector<int32_t> key(order.begin() + start, order.begin() + pos);
+            std::sort(key.begin(), key.end());
+            if (!seen.insert(key).second) continue;
+            set_rows.insert(set_rows.end(), order.begin() + start, order.begin() + pos);
+            set_ptr.push_back((int32_t)set_rows.size());
+            ++found;
+        }
+    }
+    if (found < R)
+        return fail(MBBP_E_NOT_FOUND, "only " + std::to_string(found) +
+                                          " distinct subtrees exist among the first " +
+                                          std::to_string(kMaxPerms) + " root orders");
+    return MBBP_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set_ptr,
+                       const int32_t* set_rows, mbbp_bases** out) {
+    if (!out) return fail(MBBP_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (R < 1 || R > MBBP_MAX_R) return fail(MBBP_E_INVALID, "R must be in [1, 64]");
+    if (!set_ptr || (set_ptr[R] > 0 && !set_rows)) return fail(MBBP_E_INVALID, "sets are NULL");
+    Tanner g;
+    if (mbbp_status st = make_tanner(H, m, n, g)) return st;
+    int dc = 0;
+    bool regular = true;
+    for (int r = 0; r < m; ++r) dc = std::max(dc, (int)g.rcols[r].size());
+    for (int r = 0; r < m; ++r) regular = regular && ((int)g.rcols[r].size() == dc);
+    if (dc < 1) return fail(MBBP_E_INVALID, "H has no nonzero entry");
+    if (set_ptr[0] != 0) return fail(MBBP_E_INVALID, "set_ptr[0] must be 0");
+    int maxM = 0;
+    for (int t = 0; t < R; ++t) {
+        if (set_ptr[t + 1] < set_ptr[t]) return fail(MBBP_E_INVALID, "set_ptr must be non-decreasing");
+        for (int i = set_ptr[t]; i < set_ptr[t + 1]; ++i)
+            if (set_rows[i] < 0 || set_rows[i] >= m) return fail(MBBP_E_INVALID, "set row out of range");
+        maxM = std::max(maxM, m + set_ptr[t + 1] - set_ptr[t]);
+    }
+    if (maxM > 1024) return fail(MBBP_E_TOO_LARGE, "a representation has more than 1024 rows");
+    // Variable degrees in every H^(t).
+    int dv = 0;
+    for (int t = 0; t < R; ++t) {
+        std::vector<int> deg(n, 0);
+        for (int r = 0; r < m; ++r)
+            for (int v : g.rcols[r]) ++deg[v];
+        for (int i = set_ptr[t]; i < set_ptr[t + 1]; ++i)
+            for (int v : g.rcols[set_rows[i]]) ++deg[v];
+        for (int v = 0; v < n; ++v) dv = std::max(dv, deg[v]);
+    }
+    const int need = std::max(dc, dv);
+    int K = 0;
+    for (int cand : {6, 8, 12})
+        if (need <= cand) { K = cand; break; }
+    if (K == 0) return fail(MBBP_E_TOO_LARGE, "row or column weight above 12");
+    const int MP = round_up(maxM, 32);
+    if ((long long)K * MP > MBBP_MAX_SLOTS) return fail(MBBP_E_TOO_LARGE, "too many edge slots");
+    const int mpad = round_up(m, 32), W = words_for(n);
+
+    mbbp_bases* B = new (std::nothrow) mbbp_bases();
+    if (!B) return fail(MBBP_E_NOMEM, "host allocation failed");
+    B->m = m; B->n = n; B->R = R; B->K = K; B->DV = dv; B->MP = MP; B->mpad = mpad;
+    B->W = W; B->regular = regular ? 1 : 0;
+    B->H.assign(H, H + (size_t)m * n);
+    B->set_ptr.assign(set_ptr, set_ptr + R + 1);
+    B->set_rows.assign(set_rows ? set_rows : set_ptr, set_rows ? set_rows + set_ptr[R] : set_ptr);
+
+    std::vector<uint32_t> rowinfo((size_t)R * MP, 0);
+    std::vector<uint2> vdesc((size_t)R * n);
+    std::vector<uint16_t> vslot;
+    std::vector<int32_t> rows(R), edges(R);
+    for (int t = 0; t < R; ++t) {
+        const int extra = set_ptr[t + 1] - set_ptr[t];
+        const int M = m + extra;
+        rows[t] = M;
+        std::vector<std::vector<uint16_t>> vl(n);
+        int E = 0;
+        for (int r = 0; r < M; ++r) {
+            const int src = r < m ? r : set_rows[set_ptr[t] + (r - m)];
+            const auto& cols = g.rcols[src];
+            rowinfo[(size_t)t * MP + r] = (uint32_t)src | ((uint32_t)cols.size() << 16) | (1u << 31);
+            for (int j = 0; j < (int)cols.size(); ++j) vl[cols[j]].push_back((uint16_t)(j * MP + r));
+            E += (int)cols.size();
+        }
+        edges[t] = E;
+        std::vector<int> ord(n);
+        for (int v = 0; v < n; ++v) ord[v] = v;
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int a, int b) { return vl[a].size() < vl[b].size(); });
+        for (int p = 0; p < n; ++p) {
+            const int v = ord[p];
+            uint2 d;
+            d.x = (uint32_t)vslot.size();
+            d.y = (uint32_t)v | ((uint32_t)vl[v].size() << 16);
+            vdesc[(size_t)t * n + p] = d;
+            vslot.insert(vslot.end(), vl[v].begin(), vl[v].end());
+        }
+    }
+    std::vector<uint16_t> hcol((size_t)K * mpad, (uint16_t)n);
+    std::vector<uint32_t> hmask((size_t)m * W, 0);
+    for (int r = 0; r < m; ++r)
+        for (int j = 0; j < (int)g.rcols[r].size(); ++j) {
+            const int v = g.rcols[r][j];
+            hcol[(size_t)j * mpad + r] = (uint16_t)v;
+            hmask[(size_t)r * W + (v >> 5)] |= 1u << (v & 31);
+        }
+    B->rows = rows;
+    B->edges = edges;
+
+    // One device allocation for all tables.
+    const size_t o_rowinfo = 0;
+    const size_t o_vdesc = o_rowinfo + align256(rowinfo.size() * 4);
+    const size_t o_vslot = o_vdesc + align256(vdesc.size() * sizeof(uint2));
+    const size_t o_rows = o_vslot + align256(std::max<size_t>(vslot.size(), 1) * 2);
+    const size_t o_hcol = o_rows + align256(rows.size() * 4);
+    const size_t o_hmask = o_hcol + align256(hcol.size() * 2);
+    const size_t total = o_hmask + align256(hmask.size() * 4);
+    cudaError_t e = cudaGetDevice(&B->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
+    if (e == cudaSuccess) e = cudaMalloc(&B->dmem, total);
+    if (e != cudaSuccess) {
+        delete B;
+        return cuda_fail(e, "mbbp_build_bases");
+    }
+    char* base = static_cast<char*>(B->dmem);
+    struct Copy { size_t off; const void* src; size_t bytes; } copies[] = {
+        {o_rowinfo, rowinfo.data(), rowinfo.size() * 4},
+        {o_vdesc, vdesc.data(), vdesc.size() * sizeof(uint2)},
+        {o_vslot, vslot.data(), vslot.size() * 2},
+        {o_rows, rows.data(), rows.size() * 4},
+        {o_hcol, hcol.data(), hcol.size() * 2},
+        {o_hmask, hmask.data(), hmask.size() * 4},
+    };
+    for (const Copy& c : copies) {
+        if (c.bytes == 0) continue;
+        e = cudaMemcpy(base + c.off, c.src, c.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(B->dmem);
+            delete B;
+            return cuda_fail(e, "mbbp_build_bases copy");
+        }
+    }
+    DevBases& d = B->dev;
+    d.rowinfo = reinterpret_cast<const uint32_t*>(base + o_rowinfo);
+    d.vdesc = reinterpret_cast<const uint2*>(base + o_vdesc);
+    d.vslot = reinterpret_cast<const uint16_t*>(base + o_vslot);
+    d.rows = reinterpret_cast<const int32_t*>(base + o_rows);
+    d.hcol = reinterpret_cast<const uint16_t*>(base + o_hcol);
+    d.hmask = reinterpret_cast<const uint32_t*>(base + o_hmask);
+    d.m = m; d.n = n; d.R = R; d.DC = K; d.DV = dv; d.MP = MP; d.mpad = mpad; d.W = W;
+    d.regular = B->regular;
+    *out = B;
+    return MBBP_OK;
+}
+
+mbbp_status check_device(int device) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (cur != device) return fail(MBBP_E_INVALID, "handle belongs to another device");
+    return MBBP_OK;
+}
+
+// GF(2) row reduction on bit-packed rows (uint64 words).
+struct Gf2Rows {
+    int n = 0, words = 0;
+    std::vector<std::vector<uint64_t>> rows;  // reduced rows
+    std::vector<int> pivots;                  // pivot column of each row
+    explicit Gf2Rows(int n_) : n(n_), words((n_ + 63) / 64) {}
+    static bool get(const std::vector<uint64_t>& x, int c) { return (x[c >> 6] >> (c & 63)) & 1ull; }
+    void reduce(std::vector<uint64_t>& x) const {
+        for (size_t i = 0; i < rows.size(); ++i)
+            if (get(x, pivots[i]))
+                for (int w = 0; w < words; ++w) x[w] ^= rows[i][w];
+    }
+    // Adds x if it is independent; returns whether it was.
+    bool insert(std::vector<uint64_t> x) {
+        reduce(x);
+        int piv = -1;
+        for (int c = 0; c < n && piv < 0; ++c)
+            if (get(x, c)) piv = c;
+        if (piv < 0) return false;
+        for (size_t i = 0; i < rows.size(); ++i)
+            if (get(rows[i], piv))
+                for (int w = 0; w < words; ++w) rows[i][w] ^= x[w];
+        rows.push_back(std::move(x));
+        pivots.push_back(piv);
+        return true;
+    }
+};
+
+std::vector<uint64_t> pack_row(const uint8_t* row, int n) {
+    std::vector<uint64_t> x((n + 63) / 64, 0);
+    for (int c = 0; c < n; ++c)
+        if (row[c]) x[c >> 6] |= 1ull << (c & 63);
+    return x;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mbbp_last_error(void) { return g_err.c_str(); }
+
+const char* mbbp_version(void) { return "mbbp-gb300 0.1 (sm_103a)"; }
+
+mbbp_status mbbp_permutation(uint64_t seed, int j, int m, int32_t* perm) {
+    if (!perm || m < 1 || j < 0) return fail(MBBP_E_INVALID, "mbbp_permutation: bad arguments");
+    permutation_impl(seed, j, m, perm);
+    return MBBP_OK;
+}
+
+mbbp_status mbbp_subtrees(const uint8_t* H, int m, int n, const int32_t* perm,
+                          int32_t* check_sets, int32_t* order, int32_t* n_subtrees) {
+    if (!perm || !check_sets) return fail(MBBP_E_INVALID, "mbbp_subtrees: NULL argument");
+    Tanner g;
+    if (mbbp_status st = make_tanner(H, m, n, g)) return st;
+    std::vector<char> seen(m, 0);
+    for (int i = 0; i < m; ++i) {
+        if (perm[i] < 0 || perm[i] >= m || seen[perm[i]])
+            return fail(MBBP_E_INVALID, "perm is not a permutation of 0..m-1");
+        seen[perm[i]] = 1;
+    }
+    const int s = subtrees_impl(g, perm, check_sets, order);
+    if (n_subtrees) *n_subtrees = s;
+    return MBBP_OK;
+}
+
+mbbp_status mbbp_collect_subtrees(const uint8_t* H, int m, int n, int R, uint64_t seed,
+                                  int32_t* set_ptr, int32_t* set_rows) {
+    if (!set_ptr || !set_rows) return fail(MBBP_E_INVALID, "mbbp_collect_subtrees: NULL output");
+    if (R < 1 || R > MBBP_MAX_R) return fail(MBBP_E_INVALID, "R must be in [1, 64]");
+    Tanner g;
+    if (mbbp_status st = make_tanner(H, m, n, g)) return st;
+    std::vector<int32_t> ptr, rows;
+    if (mbbp_status st = collect_impl(g, R, seed, ptr, rows)) return st;
+    std::copy(ptr.begin(), ptr.end(), set_ptr);
+    std::copy(rows.begin(), rows.end(), set_rows);
+    return MBBP_OK;
+}
+
+mbbp_status mbbp_build_bases(const uint8_t* H, int m, int n, int R, uint64_t seed,
+                             mbbp_bases** out) {
+    if (out) *out = nullptr;
+    if (R < 1 || R > MBBP_MAX_R) return fail(MBBP_E_INVALID, "R must be in [1, 64]");
+    Tanner g;
+    if (mbbp_status st = make_tanner(H, m, n, g)) return st;
+    std::vector<int32_t> ptr, rows;
+    if (mbbp_status st = collect_impl(g, R, seed, ptr, rows)) return st;
+    return build_impl(H, m, n, R, ptr.data(), rows.data(), out);
+}
+
+mbbp_status mbbp_build_bases_from_sets(const uint8_t* H, int m, int n, int R,
+                                       const int32_t* set_ptr, const int32_t* set_rows,
+                                       mbbp_bases** out) {
+    return build_impl(H, m, n, R, set_ptr, set_rows, out);
+}
+
+mbbp_status mbbp_bases_info(const mbbp_bases* B, int32_t* m, int32_t* n, int32_t* R,
+                            int32_t* rows, int32_t* edges, int32_t* set_ptr, int32_t* set_rows) {
+    if (!B) return fail(MBBP_E_INVALID, "mbbp_bases_info: NULL handle");
+    if (m) *m = B->m;
+    if (n) *n = B->n;
+    if (R) *R = B->R;
+    if (rows) std::copy(B->rows.begin(), B->rows.end(), rows);
+    if (edges) std::copy(B->edges.begin(), B->edges.end(), edges);
+    if (set_ptr) std::copy(B->set_ptr.begin(), B->set_ptr.end(), set_ptr);
+    if (set_rows) std::copy(B->set_rows.begin(), B->set_rows.end(), set_rows);
+    return MBBP_OK;
+}
+
+void mbbp_bases_free(mbbp_bases* B) {
+    if (!B) return;
+    if (B->dmem) cudaFree(B->dmem);
+    delete B;
+}
+
+mbbp_status mbbp_sample_errors(int n, int batch, uint64_t first_shot, uint64_t seed, double p,
+                               int noise, uint32_t* ex, uint32_t* ez, void* stream) {
+    if (n < 1 || n > MBBP_MAX_N || batch < 0) return fail(MBBP_E_INVALID, "mbbp_sample_errors: bad sizes");
+    if (!(p >= 0.0 && p < 1.0)) return fail(MBBP_E_INVALID, "p must be in [0, 1)");
+    if (noise != MBBP_NOISE_BSC && noise != MBBP_NOISE_DEPOLARIZING)
+        return fail(MBBP_E_INVALID, "unknown noise model");
+    if (!ex) return fail(MBBP_E_INVALID, "ex is NULL");
+    if (batch == 0) return MBBP_OK;
+    const uint64_t T = (uint64_t)std::ldexp(p, 64);
+    cudaError_t e = launch_sample(n, batch, first_shot, seed, T, noise, ex, ez, (cudaStream_t)stream);
+    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_sample_errors");
+}
+
+mbbp_status mbbp_syndrome(const mbbp_bases* B, int batch, const uint32_t* e, uint8_t* s,
+                          void* stream) {
+    if (!B || batch < 0) return fail(MBBP_E_INVALID, "mbbp_syndrome: bad arguments");
+    if (batch == 0) return MBBP_OK;
+    if (!e || !s) return fail(MBBP_E_INVALID, "mbbp_syndrome: NULL buffer");
+    if (mbbp_status st = check_device(B->device)) return st;
+    cudaError_t err = launch_syndrome(B->dev, batch, e, s, (cudaStream_t)stream);
+    return err == cudaSuccess ? MBBP_OK : cuda_fail(err, "mbbp_syndrome");
+}
+
+size_t mbbp_decode_workspace_size(const mbbp_bases* B, int batch) {
+    if (!B || batch < 0) return 0;
+    return align256((size_t)batch * B->R * B->W * 4) + 256;
+}
+
+mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                        const float* llr, int llr_stride, int iters, float alpha, int rule,
+                        uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,
+                        int16_t* selected, float* posterior, void* workspace,
+                        size_t workspace_bytes, void* stream) {
+    if (!B) return fail(MBBP_E_INVALID, "mbbp_decode: NULL handle");
+    if (batch < 0) return fail(MBBP_E_INVALID, "batch must be >= 0");
+    if (iters < 0 || iters > MBBP_MAX_ITERS) return fail(MBBP_E_INVALID, "iters out of range");
+    if (rule != MBBP_RULE_NMS && rule != MBBP_RULE_SP) return fail(MBBP_E_INVALID, "unknown rule");
+    if (rule == MBBP_RULE_NMS && !(alpha > 0.f && alpha <= 1.f))
+        return fail(MBBP_E_INVALID, "alpha must be in (0, 1]");
+    if (llr_stride != 0 && llr_stride < B->n) return fail(MBBP_E_INVALID, "llr_stride must be 0 or >= n");
+    if (batch == 0) return MBBP_OK;
+    if (!syndromes || !llr || !e_hat || !conv || !success || !workspace)
+        return fail(MBBP_E_INVALID, "mbbp_decode: NULL buffer");
+    if (workspace_bytes < mbbp_decode_workspace_size(B, batch))
+        return fail(MBBP_E_INVALID, "workspace too small");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(MBBP_E_INVALID, "workspace must be 256-byte aligned");
+    if (mbbp_status st = check_device(B->device)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    DecodeArgs a{};
+    a.B = B->dev;
+    a.synd = syndromes;
+    a.llr = llr;
+    a.llr_stride = llr_stride;
+    a.batch = batch;
+    a.iters = iters;
+    a.rule = rule;
+    a.alpha = alpha;
+    const size_t cand_bytes = align256((size_t)batch * B->R * B->W * 4);
+    a.cand = static_cast<uint32_t*>(workspace);
+    a.counter = reinterpret_cast<unsigned long long*>(static_cast<char*>(workspace) + cand_bytes);
+    a.conv = conv;
+    a.iters_run = iters_run;
+    a.post = posterior;
+    a.total_items = (unsigned long long)batch * B->R;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = launch_decode(a, s, B->sm_count);
+    if (e != cudaSuccess) return cuda_fail(e, "mbbp_decode (BP)");
+    FwsArgs f{};
+    f.cand = a.cand;
+    f.conv = conv;
+    f.batch = batch;
+    f.R = B->R;
+    f.n = B->n;
+    f.W = B->W;
+    f.e_hat = e_hat;
+    f.success = success;
+    f.selected = selected;
+    e = launch_fws(f, s);
+    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_decode (FWS)");
+}
+
+mbbp_status mbbp_logicals_build(const uint8_t* H, int m, const uint8_t* H_other, int m_other,
+                                int n, mbbp_logicals** out) {
+    if (!out) return fail(MBBP_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!H_other || m_other < 1) return fail(MBBP_E_INVALID, "H_other is empty");
+    Tanner g, go;
+    if (mbbp_status st = make_tanner(H, m, n, g)) return st;
+    if (mbbp_status st = make_tanner(H_other, m_other, n, go)) return st;
+    int dc = 0;
+    for (int r = 0; r < m; ++r) dc = std::max(dc, (int)g.rcols[r].size());
+    if (dc > MBBP_MAX_ROW_WEIGHT) return fail(MBBP_E_TOO_LARGE, "row weight above 12");
+    // ker(H_other): reduced row echelon form of H_other, one vector per free column.
+    Gf2Rows ech(n);
+    for (int r = 0; r < m_other; ++r) ech.insert(pack_row(H_other + (size_t)r * n, n));
+    std::vector<int> is_pivot(n, -1);
+    for (size_t i = 0; i < ech.rows.size(); ++i) is_pivot[ech.pivots[i]] = (int)i;
+    // rowspace(H), then add kernel vectors that are independent of it.
+    Gf2Rows span(n);
+    for (int r = 0; r < m; ++r) span.insert(pack_row(H + (size_t)r * n, n));
+    const int rank_h = (int)span.rows.size();
+    std::vector<std::vector<uint64_t>> logicals;
+    for (int f = 0; f < n; ++f) {
+        if (is_pivot[f] >= 0) continue;
+        std::vector<uint64_t> x((n + 63) / 64, 0);
+        x[f >> 6] |= 1ull << (f & 63);
+        for (size_t i = 0; i < ech.rows.size(); ++i)
+            if (Gf2Rows::get(ech.rows[i], f)) {
+                const int c = ech.pivots[i];
+                x[c >> 6] |= 1ull << (c & 63);
+            }
+        if (span.insert(x)) logicals.push_back(x);
+    }
+    const int k = (int)logicals.size();
+    if (k != n - rank_h - (int)ech.rows.size())
+        return fail(MBBP_E_INVALID, "H H_other^T != 0: not a CSS pair");
+    mbbp_logicals* L = new (std::nothrow) mbbp_logicals();
+    if (!L) return fail(MBBP_E_NOMEM, "host allocation failed");
+    const int K = dc <= 6 ? 6 : (dc <= 8 ? 8 : 12);
+    L->m = m; L->n = n; L->k = k; L->K = K; L->mpad = round_up(m, 32); L->W = words_for(n);
+    L->ops.assign((size_t)k * n, 0);
+    std::vector<uint32_t> lmask((size_t)std::max(k, 1) * L->W, 0);
+    for (int i = 0; i < k; ++i)
+        for (int c = 0; c < n; ++c)
+            if (Gf2Rows::get(logicals[i], c)) {
+                L->ops[(size_t)i * n + c] = 1;
+                lmask[(size_t)i * L->W + (c >> 5)] |= 1u << (c & 31);
+            }
+    std::vector<uint16_t> hcol((size_t)K * L->mpad, (uint16_t)n);
+    for (int r = 0; r < m; ++r)
+        for (int j = 0; j < (int)g.rcols[r].size(); ++j) hcol[(size_t)j * L->mpad + r] = (uint16_t)g.rcols[r][j];
+    const size_t o_l = align256(hcol.size() * 2);
+    const size_t total = o_l + align256(lmask.size() * 4);
+    cudaError_t e = cudaGetDevice(&L->device);
+    if (e == cudaSuccess) e = cudaMalloc(&L->dmem, total);
+    if (e == cudaSuccess) e = cudaMemcpy(L->dmem, hcol.data(), hcol.size() * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(static_cast<char*>(L->dmem) + o_l, lmask.data(), lmask.size() * 4,
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (L->dmem) cudaFree(L->dmem);
+        delete L;
+        return cuda_fail(e, "mbbp_logicals_build");
+    }
+    L->dev.hcol = static_cast<const uint16_t*>(L->dmem);
+    L->dev.lmask = reinterpret_cast<const uint32_t*>(static_cast<char*>(L->dmem) + o_l);
+    L->dev.m = m; L->dev.n = n; L->dev.k = k; L->dev.DC = K; L->dev.mpad = L->mpad; L->dev.W = L->W;
+    *out = L;
+    return MBBP_OK;
+}
+
+mbbp_status mbbp_logicals_info(const mbbp_logicals* L, int32_t* k, uint8_t* ops) {
+    if (!L) return fail(MBBP_E_INVALID, "mbbp_logicals_info: NULL handle");
+    if (k) *k = L->k;
+    if (ops) std::copy(L->ops.begin(), L->ops.end(), ops);
+    return MBBP_OK;
+}
+
+mbbp_status mbbp_judge(const mbbp_logicals* L, int batch, const uint32_t* e, const uint8_t* e_hat,
+                       uint8_t* fail_out, unsigned long long* counts, void* stream) {
+    if (!L || batch < 0) return fail(MBBP_E_INVALID, "mbbp_judge: bad arguments");
+    if (batch == 0) return MBBP_OK;
+    if (!e || !e_hat) return fail(MBBP_E_INVALID, "mbbp_judge: NULL buffer");
+    if (mbbp_status st = check_device(L->device)) return st;
+    cudaError_t err = launch_judge(L->dev, batch, e, e_hat, fail_out, counts, (cudaStream_t)stream);
+    return err == cudaSuccess ? MBBP_OK : cuda_fail(err, "mbbp_judge");
+}
+
+void mbbp_logicals_free(mbbp_logicals* L) {
+    if (!L) return;
+    if (L->dmem) cudaFree(L->dmem);
+    delete L;
+}
+
+}  // extern "C"

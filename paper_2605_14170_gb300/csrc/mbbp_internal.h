@@ -1,0 +1,76 @@
+// Internal layout shared by the host library (host.cpp) and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mbbp.h"
+
+namespace mbbp {
+
+constexpr int kWarpsPerBlock = 8;
+
+inline int words_for(int n) { return (n + 31) / 32; }
+inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// Device copy of the R representations of one code.  Rows of H^(t) are laid
+// out ELL-style: the j-th edge of row r of representation t is "slot"
+// j * MP + r of that representation's message array, so lane r of a warp
+// reads the j-th message of its row with unit stride across the warp.
+struct DevBases {
+    const uint32_t* rowinfo;  // [R][MP] src row (bits 0-15) | degree (16-23) | valid (bit 31)
+    const uint2* vdesc;       // [R][n]  x = first slot-list entry, y = variable | degree << 16;
+                              //         variables sorted by degree (stable)
+    const uint16_t* vslot;    // slot ids of every variable, ascending row of H^(t)
+    const int32_t* rows;      // [R] rows of H^(t)
+    const uint16_t* hcol;     // [DC][mpad] columns of the rows of H (n = padding)
+    const uint32_t* hmask;    // [m][W] rows of H as bit masks
+    int m, n, R, DC, DV, MP, mpad, W;
+    int regular;              // every row of H has weight DC
+};
+
+struct DecodeArgs {
+    DevBases B;
+    const uint8_t* synd;      // [batch][m]
+    const float* llr;         // [n] or [batch][llr_stride]
+    int llr_stride;
+    int batch, iters, rule;
+    float alpha;
+    uint32_t* cand;           // [batch][R][W]
+    uint8_t* conv;            // [batch][R]
+    uint16_t* iters_run;      // [batch][R] or null
+    float* post;              // [batch][R][n] or null
+    unsigned long long* counter;
+    unsigned long long total_items;
+};
+
+struct FwsArgs {
+    const uint32_t* cand;
+    const uint8_t* conv;
+    int batch, R, n, W;
+    uint8_t* e_hat;
+    uint8_t* success;
+    int16_t* selected;
+};
+
+struct DevLogicals {
+    const uint16_t* hcol;     // [DC][mpad]
+    const uint32_t* lmask;    // [k][W]
+    int m, n, k, DC, mpad, W;
+};
+
+// Launchers (decode.cu, aux.cu).  They return cudaGetLastError().
+cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_fws(const FwsArgs& a, cudaStream_t s);
+size_t decode_smem_bytes(const DevBases& B, int warps);
+cudaError_t launch_sample(int n, int batch, uint64_t first_shot, uint64_t seed, uint64_t T,
+                          int noise, uint32_t* ex, uint32_t* ez, cudaStream_t s);
+cudaError_t launch_syndrome(const DevBases& B, int batch, const uint32_t* e, uint8_t* synd,
+                            cudaStream_t s);
+cudaError_t launch_judge(const DevLogicals& L, int batch, const uint32_t* e,
+                         const uint8_t* e_hat, uint8_t* fail, unsigned long long* counts,
+                         cudaStream_t s);
+
+}  // namespace mbbp

@@ -1,0 +1,336 @@
+"""Python binding of the C ABI in ``include/mbbp.h`` (ctypes).
+
+Argument marshalling only: every step of the decoder runs in ``libmbbp.so``.
+The functions keep the C names.  Host arrays are numpy arrays; device buffers
+are CUDA torch tensors (torch provides the memory and the current stream).
+Packed bit vectors (uint32 words in the ABI) are held in int32 tensors,
+uint16 outputs in int16 tensors and uint64 counters in int64 tensors, with
+the same bits.
+
+There is no CPU fallback: importing this module raises if the library has
+not been built, and every non-OK status raises ``MBBPError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmbbp.so")
+
+RULE_NMS = 0
+RULE_SP = 1
+NOISE_BSC = 0
+NOISE_DEPOLARIZING = 1
+MAX_R = 64
+LMAX = 1.0e4
+PMAX = 1.0 - 2.0 ** -23
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = C.CDLL(LIB_PATH)
+
+
+class MBBPError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.mbbp_last_error().decode()
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C")
+_vp = C.c_void_p
+_sig = {
+    "mbbp_last_error": (C.c_char_p, []),
+    "mbbp_version": (C.c_char_p, []),
+    "mbbp_permutation": (C.c_int, [C.c_uint64, C.c_int, C.c_int, _i32p]),
+    "mbbp_subtrees": (C.c_int, [_u8p, C.c_int, C.c_int, _i32p, _i32p, _vp, _vp]),
+    "mbbp_collect_subtrees": (C.c_int, [_u8p, C.c_int, C.c_int, C.c_int, C.c_uint64, _i32p, _i32p]),
+    "mbbp_build_bases": (C.c_int, [_u8p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_vp)]),
+    "mbbp_build_bases_from_sets": (C.c_int, [_u8p, C.c_int, C.c_int, C.c_int, _i32p, _i32p,
+                                             C.POINTER(_vp)]),
+    "mbbp_bases_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mbbp_bases_free": (None, [_vp]),
+    "mbbp_sample_errors": (C.c_int, [C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
+                                     _vp, _vp, _vp]),
+    "mbbp_syndrome": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "mbbp_decode_workspace_size": (C.c_size_t, [_vp, C.c_int]),
+    "mbbp_decode": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
+                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "mbbp_logicals_build": (C.c_int, [_u8p, C.c_int, _u8p, C.c_int, C.c_int, C.POINTER(_vp)]),
+    "mbbp_logicals_info": (C.c_int, [_vp, _vp, _vp]),
+    "mbbp_judge": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "mbbp_logicals_free": (None, [_vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise MBBPError(status, where)
+
+
+def _u8(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.uint8)
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dptr(t, dtype=None, name="buffer"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def mbbp_version() -> str:
+    return _lib.mbbp_version().decode()
+
+
+def mbbp_last_error() -> str:
+    return _lib.mbbp_last_error().decode()
+
+
+# ----------------------------------------------------------------- host only
+
+def mbbp_permutation(seed: int, j: int, m: int) -> np.ndarray:
+    perm = np.zeros(m, np.int32)
+    _check(_lib.mbbp_permutation(seed, j, m, perm), "mbbp_permutation")
+    return perm
+
+
+def mbbp_subtrees(H, perm):
+    """Algorithm 2: (check_sets 1-based, acceptance order, number of subtrees)."""
+    H = _u8(H)
+    m, n = H.shape
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    cs = np.zeros(m, np.int32)
+    order = np.zeros(m, np.int32)
+    ns = C.c_int32(0)
+    _check(_lib.mbbp_subtrees(H, m, n, perm, cs, _np_ptr(order), C.cast(C.pointer(ns), C.c_void_p)),
+           "mbbp_subtrees")
+    return cs, order, int(ns.value)
+
+
+def mbbp_collect_subtrees(H, R: int, seed: int):
+    """The R subtrees used as representations (row arrays in acceptance order)."""
+    H = _u8(H)
+    m, n = H.shape
+    ptr = np.zeros(R + 1, np.int32)
+    rows = np.zeros(max(R * m, 1), np.int32)
+    _check(_lib.mbbp_collect_subtrees(H, m, n, R, seed, ptr, rows), "mbbp_collect_subtrees")
+    return [rows[ptr[t]:ptr[t + 1]].copy() for t in range(R)]
+
+
+class Bases:
+    """Owner of an ``mbbp_bases`` handle (freed with the object)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+        info = mbbp_bases_info(self)
+        self.m, self.n, self.R = info["m"], info["n"], info["R"]
+        self.rows, self.edges, self.sets = info["rows"], info["edges"], info["sets"]
+        self.words = (self.n + 31) // 32
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.mbbp_bases_free(h)
+            self.handle = C.c_void_p(None)
+
+
+def mbbp_build_bases(H, R: int, seed: int) -> Bases:
+    H = _u8(H)
+    m, n = H.shape
+    out = C.c_void_p()
+    _check(_lib.mbbp_build_bases(H, m, n, R, seed, C.byref(out)), "mbbp_build_bases")
+    return Bases(out.value)
+
+
+def mbbp_build_bases_from_sets(H, sets) -> Bases:
+    H = _u8(H)
+    m, n = H.shape
+    R = len(sets)
+    ptr = np.zeros(R + 1, np.int32)
+    for t, s in enumerate(sets):
+        ptr[t + 1] = ptr[t] + len(s)
+    rows = np.ascontiguousarray(
+        np.concatenate([np.asarray(s, np.int32) for s in sets]) if ptr[-1] else np.zeros(1, np.int32),
+        dtype=np.int32)
+    out = C.c_void_p()
+    _check(_lib.mbbp_build_bases_from_sets(H, m, n, R, ptr, rows, C.byref(out)),
+           "mbbp_build_bases_from_sets")
+    return Bases(out.value)
+
+
+def mbbp_bases_info(B: Bases) -> dict:
+    m, n, R = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_lib.mbbp_bases_info(B.handle, C.cast(C.pointer(m), _vp), C.cast(C.pointer(n), _vp),
+                                C.cast(C.pointer(R), _vp), None, None, None, None), "mbbp_bases_info")
+    R_ = R.value
+    rows = np.zeros(R_, np.int32)
+    edges = np.zeros(R_, np.int32)
+    ptr = np.zeros(R_ + 1, np.int32)
+    _check(_lib.mbbp_bases_info(B.handle, None, None, None, _np_ptr(rows), _np_ptr(edges),
+                                _np_ptr(ptr), None), "mbbp_bases_info")
+    srows = np.zeros(max(int(ptr[-1]), 1), np.int32)
+    _check(_lib.mbbp_bases_info(B.handle, None, None, None, None, None, None, _np_ptr(srows)),
+           "mbbp_bases_info")
+    sets = [srows[ptr[t]:ptr[t + 1]].copy() for t in range(R_)]
+    return {"m": m.value, "n": n.value, "R": R_, "rows": rows, "edges": edges, "sets": sets}
+
+
+# ----------------------------------------------------------------- device
+
+def mbbp_sample_errors(n: int, batch: int, first_shot: int, seed: int, p: float, noise: int,
+                       ex, ez=None, stream=None) -> None:
+    """ex / ez: int32 CUDA tensors of batch * ceil(n/32) words."""
+    import torch
+    _check(_lib.mbbp_sample_errors(n, batch, first_shot, seed, float(p), noise,
+                                   _dptr(ex, torch.int32, "ex"), _dptr(ez, torch.int32, "ez"),
+                                   _stream(stream)), "mbbp_sample_errors")
+
+
+def mbbp_syndrome(B: Bases, e, s, stream=None) -> None:
+    """e: int32 [batch, W] packed errors; s: uint8 [batch, m]."""
+    import torch
+    batch = s.shape[0] if s.dim() > 1 else s.numel() // B.m
+    _check(_lib.mbbp_syndrome(B.handle, batch, _dptr(e, torch.int32, "e"),
+                              _dptr(s, torch.uint8, "s"), _stream(stream)), "mbbp_syndrome")
+
+
+def mbbp_decode_workspace_size(B: Bases, batch: int) -> int:
+    return int(_lib.mbbp_decode_workspace_size(B.handle, batch))
+
+
+def mbbp_decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int, e_hat, conv,
+                success, workspace, iters_run=None, selected=None, posterior=None,
+                stream=None) -> None:
+    """Algorithm 1 on a batch; see mbbp.h for every argument."""
+    import torch
+    batch = syndromes.shape[0]
+    if syndromes.numel() != batch * B.m:
+        raise ValueError("syndromes must be [batch, m]")
+    stride = 0 if llr.dim() == 1 else llr.shape[-1]
+    _check(_lib.mbbp_decode(
+        B.handle, batch, _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
+        stride, iters, float(alpha), rule, _dptr(e_hat, torch.uint8, "e_hat"),
+        _dptr(conv, torch.uint8, "conv"), _dptr(iters_run, torch.int16, "iters_run"),
+        _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
+        _dptr(posterior, torch.float32, "posterior"), _dptr(workspace, torch.uint8, "workspace"),
+        workspace.numel(), _stream(stream)), "mbbp_decode")
+
+
+class Logicals:
+    """Owner of an ``mbbp_logicals`` handle."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = C.c_void_p(handle)
+        self.n = n
+        k = C.c_int32()
+        _check(_lib.mbbp_logicals_info(self.handle, C.cast(C.pointer(k), _vp), None), "mbbp_logicals_info")
+        self.k = k.value
+
+    def ops(self) -> np.ndarray:
+        out = np.zeros((max(self.k, 1), self.n), np.uint8)
+        _check(_lib.mbbp_logicals_info(self.handle, None, _np_ptr(out)), "mbbp_logicals_info")
+        return out[: self.k]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.mbbp_logicals_free(h)
+            self.handle = C.c_void_p(None)
+
+
+def mbbp_logicals_build(H, H_other) -> Logicals:
+    H, Ho = _u8(H), _u8(H_other)
+    out = C.c_void_p()
+    _check(_lib.mbbp_logicals_build(H, H.shape[0], Ho, Ho.shape[0], H.shape[1], C.byref(out)),
+           "mbbp_logicals_build")
+    return Logicals(out.value, H.shape[1])
+
+
+def mbbp_judge(L: Logicals, e, e_hat, fail=None, counts=None, stream=None) -> None:
+    import torch
+    batch = e_hat.shape[0]
+    _check(_lib.mbbp_judge(L.handle, batch, _dptr(e, torch.int32, "e"), _dptr(e_hat, torch.uint8, "e_hat"),
+                           _dptr(fail, torch.uint8, "fail"), _dptr(counts, torch.int64, "counts"),
+                           _stream(stream)), "mbbp_judge")
+
+
+# ----------------------------------------------------------------- helpers
+
+def decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int = RULE_NMS,
+           want_posterior: bool = False, stream=None) -> dict:
+    """Allocate the outputs with torch and call ``mbbp_decode``.
+
+    Returns a dict of CUDA tensors: e_hat [batch, n], conv [batch, R],
+    iters [batch, R] (int16 holding uint16), success [batch], selected
+    [batch], cand [batch, R, W] (int32 words; a view of the workspace) and
+    posterior [batch, R, n] if requested."""
+    import torch
+    dev = syndromes.device
+    batch = syndromes.shape[0]
+    out = {
+        "e_hat": torch.empty((batch, B.n), dtype=torch.uint8, device=dev),
+        "conv": torch.empty((batch, B.R), dtype=torch.uint8, device=dev),
+        "iters": torch.empty((batch, B.R), dtype=torch.int16, device=dev),
+        "success": torch.empty((batch,), dtype=torch.uint8, device=dev),
+        "selected": torch.empty((batch,), dtype=torch.int16, device=dev),
+    }
+    ws_bytes = mbbp_decode_workspace_size(B, batch)
+    ws = torch.empty((ws_bytes,), dtype=torch.uint8, device=dev)
+    post = (torch.empty((batch, B.R, B.n), dtype=torch.float32, device=dev)
+            if want_posterior else None)
+    mbbp_decode(B, syndromes, llr, iters, alpha, rule, out["e_hat"], out["conv"], out["success"], ws,
+                iters_run=out["iters"], selected=out["selected"], posterior=post, stream=stream)
+    out["cand"] = ws[: batch * B.R * B.words * 4].view(torch.int32).view(batch, B.R, B.words)
+    out["workspace"] = ws
+    if want_posterior:
+        out["posterior"] = post
+    return out
+
+
+def unpack_words(words, n: int) -> np.ndarray:
+    """int32 words [..., W] (numpy or tensor) -> uint8 bits [..., n]."""
+    if hasattr(words, "cpu"):
+        words = words.cpu().numpy()
+    w = np.ascontiguousarray(words).view(np.uint32)
+    bits = ((w[..., :, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.uint8)
+    return bits.reshape(w.shape[:-1] + (w.shape[-1] * 32,))[..., :n]
+
+
+def pack_bits(bits) -> np.ndarray:
+    """uint8 bits [..., n] -> int32 words [..., ceil(n/32)]."""
+    bits = np.asarray(bits, np.uint8)
+    n = bits.shape[-1]
+    W = (n + 31) // 32
+    pad = np.zeros(bits.shape[:-1] + (W * 32,), np.uint8)
+    pad[..., :n] = bits
+    w = (pad.reshape(bits.shape[:-1] + (W, 32)).astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(-1)
+    return w.astype(np.uint32).view(np.int32)

@@ -1,0 +1,234 @@
+"""GPU decoder (mbbp_decode through the C ABI) against the oracle.
+
+Exact stages: with normalized min-sum the CUDA path reproduces the FP32
+oracle bit for bit, so every per-representation candidate, convergence flag,
+iteration count, FWS selection and final estimate must be identical on every
+shot.  Sum-product differs only through tanhf/atanhf (CUDA vs libm), so its
+decisions are compared by agreement rate and its messages by tolerance.
+Against the FP64 oracle: posterior LLRs within 1e-4 relative and hard
+decisions on >= 99.9% of shots.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_14170_gb300.inputs import channel_llr, named_code
+
+pytestmark = pytest.mark.gpu
+
+SEED = 20260514
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch  # noqa: F401
+    from paper_2605_14170_gb300 import mbbp
+    return mbbp
+
+
+def gpu_decode(M, B, s, llr, iters, alpha, rule=0, post=False):
+    import torch
+    dev = torch.device("cuda:0")
+    out = M.decode(B, torch.from_numpy(np.ascontiguousarray(s)).to(dev),
+                   torch.from_numpy(np.ascontiguousarray(llr, np.float32)).to(dev),
+                   iters, alpha, rule, want_posterior=post)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items() if k not in ("cand", "workspace")}
+    res["iters"] = res["iters"].view(np.uint16)
+    res["cand"] = M.unpack_words(out["cand"], B.n)
+    return res
+
+
+def assert_exact(got, ref):
+    assert np.array_equal(got["conv"], ref["conv"]), "convergence flags"
+    assert np.array_equal(got["iters"], ref["iters"]), "iteration counts"
+    assert np.array_equal(got["cand"], ref["cand"]), "per-representation estimates"
+    assert np.array_equal(got["selected"], ref["selected"]), "FWS selection"
+    assert np.array_equal(got["success"], ref["success"]), "success flags"
+    assert np.array_equal(got["e_hat"], ref["ehat"]), "final estimates"
+
+
+def workload(code, which, shots, p, noise, first=0, seed=SEED):
+    c = named_code(code)
+    H = getattr(c, which)
+    ex, ez = oracle.sample(seed, first, shots, H.shape[1], p, noise)
+    e = ex if which == "HZ" else ez
+    return c, H, e, oracle.syndrome(H, e)
+
+
+def test_bb72_nms_exact_2000_shots(M):
+    """[[72,12,6]], X errors p = 0.05 decoded with H_Z, R = 4, 50 iterations,
+    alpha = 0.625, 2000 shots: every output identical to the FP32 oracle."""
+    c, H, e, s = workload("bb72", "HZ", 2000, 0.05, "bsc")
+    B = M.mbbp_build_bases(H, 4, SEED)
+    assert all(np.array_equal(a, b) for a, b in zip(B.sets, oracle.collect_subtrees(H, 4, SEED)))
+    llr = channel_llr(72, 0.05).astype(np.float32)
+    got = gpu_decode(M, B, s, llr, 50, 0.625)
+    ref = oracle.mbbp_decode(H, B.sets, s, llr, 50, 0.625, precision="f32")
+    assert_exact(got, ref)
+    # the halting rule: every converged candidate satisfies its syndrome
+    ok = ((got["cand"].astype(np.int64) @ H.T.astype(np.int64)) % 2 == s[:, None, :]).all(-1)
+    assert np.array_equal(ok & (got["conv"] == 1), got["conv"] == 1)
+    # repeatable bit for bit
+    again = gpu_decode(M, B, s, llr, 50, 0.625)
+    assert_exact(again, ref)
+
+
+@pytest.mark.parametrize("which", ["HZ", "HX"])
+def test_bb144_nms_exact_r16(M, which):
+    """[[144,12,12]], depolarizing p = 0.06 (both error types), R = 16,
+    100 iterations: several tiles of rows and a ragged last word."""
+    c, H, e, s = workload("bb144", which, 200, 0.06, "depolarizing")
+    B = M.mbbp_build_bases(H, 16, SEED + 1)
+    llr = channel_llr(144, 2 * 0.06 / 3).astype(np.float32)
+    got = gpu_decode(M, B, s, llr, 100, 0.625)
+    ref = oracle.mbbp_decode(H, B.sets, s, llr, 100, 0.625, precision="f32")
+    assert_exact(got, ref)
+
+
+def test_per_shot_llrs_and_negative_llrs(M):
+    """Per-shot LLR rows (llr_stride = n), including negative LLRs whose hard
+    decision starts at 1, on the [[72,12,6]] code."""
+    c, H, e, s = workload("bb72", "HX", 300, 0.06, "depolarizing")
+    rng = np.random.default_rng(4)
+    llr = rng.uniform(-1.0, 4.0, (300, 72)).astype(np.float32)
+    B = M.mbbp_build_bases(H, 6, 3)
+    got = gpu_decode(M, B, s, llr, 30, 0.8)
+    ref = oracle.mbbp_decode(H, B.sets, s, llr, 30, 0.8, precision="f32")
+    assert_exact(got, ref)
+
+
+def test_edge_cases(M):
+    import torch
+    c, H, e, s = workload("bb72", "HZ", 64, 0.05, "bsc")
+    llr = channel_llr(72, 0.05).astype(np.float32)
+    # plain BP: one representation with no extra rows
+    B1 = M.mbbp_build_bases_from_sets(H, [[]])
+    got = gpu_decode(M, B1, s, llr, 20, 0.625)
+    assert_exact(got, oracle.mbbp_decode(H, [np.zeros(0, np.int32)], s, llr, 20, 0.625, precision="f32"))
+    # iters = 0: only the hard decision of the LLRs is tested
+    B = M.mbbp_build_bases(H, 4, 9)
+    got = gpu_decode(M, B, s, llr, 0, 0.625)
+    ref = oracle.mbbp_decode(H, B.sets, s, llr, 0, 0.625, precision="f32")
+    assert_exact(got, ref)
+    assert (got["success"] == (~s.any(1))).all()
+    # zero syndromes converge at K = 0 with e = 0
+    z = np.zeros_like(s)
+    got = gpu_decode(M, B, z, llr, 10, 0.625)
+    assert got["conv"].all() and (got["iters"] == 0).all() and got["e_hat"].sum() == 0
+    # a single shot, and arbitrary explicit rows (random augmentation)
+    rng = np.random.default_rng(1)
+    sets = [rng.choice(36, 9, replace=False) for _ in range(3)] + [[0, 0, 5]]
+    B2 = M.mbbp_build_bases_from_sets(H, sets)
+    got = gpu_decode(M, B2, s[:1], llr, 25, 0.5)
+    assert_exact(got, oracle.mbbp_decode(H, [np.asarray(x, np.int32) for x in sets], s[:1], llr, 25, 0.5,
+                                         precision="f32"))
+    # batch = 0 is a no-op
+    dev = torch.device("cuda:0")
+    out = M.decode(B, torch.zeros((0, 36), dtype=torch.uint8, device=dev),
+                   torch.from_numpy(llr).to(dev), 5, 0.625)
+    assert out["e_hat"].shape == (0, 72)
+
+
+def test_fig2_code(M):
+    """The 4 x 6 matrix of Fig. 2 with every syndrome: degree-3 rows in a
+    width-6 layout, rows shorter than the kernel width."""
+    H = np.array([[1, 1, 1, 0, 0, 0], [0, 1, 1, 0, 0, 1], [1, 0, 0, 1, 1, 0], [0, 0, 0, 1, 1, 1]], np.uint8)
+    s = np.array([[(k >> i) & 1 for i in range(4)] for k in range(16)], np.uint8)
+    llr = np.array([2.0, 1.0, 1.5, 0.5, 3.0, 2.5], np.float32)
+    B = M.mbbp_build_bases_from_sets(H, [[0, 2], [3, 1]])  # t1, t2 of Fig. 2
+    got = gpu_decode(M, B, s, llr, 10, 0.75)
+    assert_exact(got, oracle.mbbp_decode(H, B.sets, s, llr, 10, 0.75, precision="f32"))
+
+
+def test_irregular_code(M):
+    """Rows of different weight (3..8) and columns up to weight 8: the
+    width-8 kernel with per-row degrees."""
+    rng = np.random.default_rng(7)
+    m, n = 40, 90
+    H = np.zeros((m, n), np.uint8)
+    col_w = np.zeros(n, int)
+    for r in range(m):
+        avail = np.nonzero(col_w < 4)[0]
+        cols = rng.choice(avail, min(int(rng.integers(3, 9)), len(avail)), replace=False)
+        H[r, cols] = 1
+        col_w[cols] += 1
+    e = (rng.random((150, n)) < 0.04).astype(np.uint8)
+    s = oracle.syndrome(H, e)
+    sets = oracle.collect_subtrees(H, 5, 11)
+    B = M.mbbp_build_bases_from_sets(H, sets)
+    llr = channel_llr(n, 0.04).astype(np.float32)
+    got = gpu_decode(M, B, s, llr, 40, 0.7)
+    assert_exact(got, oracle.mbbp_decode(H, sets, s, llr, 40, 0.7, precision="f32"))
+
+
+def test_gb882_r64_max_size(M):
+    """Largest workload: the length-882 GB code with R = 64 (rows up to
+    441 + 176 per representation), a handful of shots."""
+    c, H, e, s = workload("gb882", "HZ", 6, 0.03, "depolarizing")
+    B = M.mbbp_build_bases(H, 64, SEED)
+    llr = channel_llr(882, 0.02).astype(np.float32)
+    got = gpu_decode(M, B, s, llr, 100, 0.625)
+    ref = oracle.mbbp_decode(H, B.sets, s, llr, 100, 0.625, precision="f32")
+    assert_exact(got, ref)
+
+
+def test_invalid_arguments(M):
+    import torch
+    c = named_code("bb72")
+    B = M.mbbp_build_bases(c.HZ, 4, 1)
+    dev = torch.device("cuda:0")
+    s = torch.zeros((4, 36), dtype=torch.uint8, device=dev)
+    llr = torch.ones(72, dtype=torch.float32, device=dev)
+    for kw in ({"alpha": 0.0}, {"alpha": 1.5}, {"iters": -1}, {"rule": 7}):
+        args = dict(iters=5, alpha=0.5, rule=0)
+        args.update(kw)
+        with pytest.raises(M.MBBPError):
+            M.decode(B, s, llr, **args)
+    ws = torch.empty(16, dtype=torch.uint8, device=dev)
+    outs = [torch.empty(4 * 72, dtype=torch.uint8, device=dev), torch.empty(16, dtype=torch.uint8, device=dev),
+            torch.empty(4, dtype=torch.uint8, device=dev)]
+    with pytest.raises(M.MBBPError):
+        M.mbbp_decode(B, s, llr, 5, 0.5, 0, outs[0], outs[1], outs[2], ws)
+    with pytest.raises(M.MBBPError):
+        M.mbbp_build_bases(c.HZ, 65, 1)
+    big = np.ones((4, 20), np.uint8)  # row weight 20 > 12
+    with pytest.raises(M.MBBPError):
+        M.mbbp_build_bases_from_sets(big, [[]])
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_fp64_messages_and_decisions(M, rule):
+    """Posterior LLRs after 1, 2 and 5 iterations within 1e-4 relative of the
+    FP64 oracle; final hard decisions on >= 99.9% of shots."""
+    c, H, e, s = workload("bb72", "HZ", 400, 0.05, "bsc", first=5000)
+    B = M.mbbp_build_bases(H, 4, SEED)
+    llr = channel_llr(72, 0.05)
+    for it in (1, 2, 5):
+        got = gpu_decode(M, B, s, llr, it, 0.625, rule, post=True)
+        ref = oracle.mbbp_decode(H, B.sets, s, llr, it, 0.625, rule, precision="f64", want_post=True)
+        same = got["iters"] == ref["iters"]  # same stopping point
+        assert same.mean() > 0.99
+        g, r = got["posterior"][same], ref["post"][same]
+        err = np.abs(g - r) / np.maximum(np.abs(r), 1.0)
+        assert err.max() <= 1e-4, (it, err.max())
+    c, H, e, s = workload("bb72", "HZ", 2000, 0.05, "bsc")
+    got = gpu_decode(M, B, s, llr, 50, 0.625, rule)
+    ref = oracle.mbbp_decode(H, B.sets, s, llr, 50, 0.625, rule, precision="f64")
+    agree = (got["e_hat"] == ref["ehat"]).all(1).mean()
+    assert agree >= 0.999, agree
+
+
+def test_sum_product_against_fp32_oracle(M):
+    """Sum-product: decisions agree with the FP32 oracle (libm vs CUDA
+    tanhf/atanhf), posteriors within 1e-4 relative where trajectories agree."""
+    c, H, e, s = workload("bb144", "HZ", 300, 0.05, "depolarizing")
+    B = M.mbbp_build_bases(H, 8, 2)
+    llr = channel_llr(144, 2 * 0.05 / 3).astype(np.float32)
+    got = gpu_decode(M, B, s, llr, 60, 1.0, 1, post=True)
+    ref = oracle.mbbp_decode(H, B.sets, s, llr, 60, 1.0, 1, precision="f32", want_post=True)
+    assert (got["e_hat"] == ref["ehat"]).all(1).mean() >= 0.99
+    assert (got["conv"] == ref["conv"]).mean() >= 0.99
+    same = got["iters"] == ref["iters"]
+    err = np.abs(got["posterior"][same] - ref["post"][same]) / np.maximum(np.abs(ref["post"][same]), 1.0)
+    assert np.quantile(err, 0.999) <= 1e-4
