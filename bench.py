@@ -254,7 +254,7 @@ def main():
                     dec_events.append((ev0, ev1, key))
                 mbbp.mbbp_judge(L, e, e_hat, fl, counts[ip, 0 if key == "Z" else 1])
                 launches += 4  # syndrome, BP, FWS, judge
-                work.add_((iters.to(torch.int64) & 0xFFFF).sum(0) @ edges[key])
+                work.add_(((iters.to(torch.int64) & 0xFFFF).sum(0) * edges[key]).sum())
             # any-type failure for the combined logical error rate
             counts[ip, 2, 1] += ((fail_x != 0) | (fail_z != 0)).sum()
         launches_per_step = launches

@@ -57,15 +57,18 @@ enum { MBBP_NOISE_BSC = 0,          /* independent X errors (Section IV)     */
 #define MBBP_MAX_N 16384       /* variables (qubits)                           */
 #define MBBP_MAX_ROW_WEIGHT 12 /* check degree d_c of H                        */
 #define MBBP_MAX_COL_WEIGHT 12 /* variable degree in any H^(t)                 */
+#define MBBP_MAX_ROWS 1024     /* rows of any H^(t) = m + |t|                   */
 #define MBBP_MAX_SLOTS 65536   /* d_c * (rows of the largest H^(t), padded to 32) */
 #define MBBP_MAX_ITERS 65535
 
 /* Readings of the paper that the kernels fix (the paper states none):
  * v->c messages are clamped to [-MBBP_LMAX, MBBP_LMAX]; the min of Eq. (2)
  * also runs over MBBP_LMAX (a degree-1 row sends alpha*LMAX); sum-product
- * products are clamped to [-MBBP_PMAX, MBBP_PMAX] before atanh. */
+ * check messages are evaluated as phi(sum phi(|q|)) with Gallager's
+ * phi(x) = log((e^x+1)/(e^x-1)) and clamped to MBBP_SP_MAX = 2 atanh(1 - 2^-23)
+ * in magnitude. */
 #define MBBP_LMAX 1.0e4f
-#define MBBP_PMAX (1.0f - 1.0f / 8388608.0f)
+#define MBBP_SP_MAX 16.635532f
 
 typedef struct mbbp_bases mbbp_bases;
 typedef struct mbbp_logicals mbbp_logicals;

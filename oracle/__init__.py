@@ -44,7 +44,7 @@ _lock = threading.Lock()
 RULE_NMS = 0
 RULE_SP = 1
 LMAX = 1.0e4
-PMAX = 1.0 - 2.0 ** -23
+SPMAX = 16.635532333438686  # 2 atanh(1 - 2^-23)
 
 
 def build(force: bool = False) -> str:

@@ -36,8 +36,12 @@
 #define OR_RULE_SP 1
 /* Message clamp (not stated in the paper; see bp_body.inc). */
 #define OR_LMAX 1.0e4
-/* Sum-product product clamp, 1 - 2^-23 (exact in float and double). */
-#define OR_PMAX (1.0 - 1.0 / 8388608.0)
+/* Sum-product magnitude clamp: 2 atanh(1 - 2^-23) = ln(2^24 - 1). */
+#define OR_SPMAX 16.635532333438686
+
+/* Gallager's phi(x) = log((e^x + 1) / (e^x - 1)) = log1p(2 / expm1(x)). */
+static double or_phi64(double x) { return log1p(2.0 / expm1(x)); }
+static float or_phi32(float x) { return log1pf(2.0f / expm1f(x)); }
 
 /* ------------------------------------------------------------------ RNG -- */
 
@@ -299,29 +303,25 @@ int or_fws(const uint8_t* cand, const uint8_t* conv, int R, int n,
 #define BP_FN or_bp_f64
 #define DECODE_FN or_mbbp_decode_f64
 #define FABS fabs
-#define TANH tanh
-#define ATANH atanh
+#define PHI or_phi64
 #include "bp_body.inc"
 #undef REAL
 #undef BP_FN
 #undef DECODE_FN
 #undef FABS
-#undef TANH
-#undef ATANH
+#undef PHI
 
 #define REAL float
 #define BP_FN or_bp_f32
 #define DECODE_FN or_mbbp_decode_f32
 #define FABS fabsf
-#define TANH tanhf
-#define ATANH atanhf
+#define PHI or_phi32
 #include "bp_body.inc"
 #undef REAL
 #undef BP_FN
 #undef DECODE_FN
 #undef FABS
-#undef TANH
-#undef ATANH
+#undef PHI
 
 /* Exported single-instance entry points (BP on one representation). */
 void or_bp_one_f64(const uint8_t* Ht, int M, int n, const uint8_t* st,

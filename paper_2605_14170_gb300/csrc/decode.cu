@@ -15,11 +15,11 @@
 //
 // Arithmetic.  Every float operation is a correctly rounded intrinsic
 // (__fadd_rn / __fmul_rn) in the order the oracle uses: variable sums in
-// ascending row order of H^(t) excluding the own edge, sum-product products
+// ascending row order of H^(t) excluding the own edge, sum-product phi sums
 // in ascending column order excluding the own edge.  Min-sum takes its min
 // over the other edges and MBBP_LMAX with a min1/min2 pair, which gives the
 // same value as the direct min.  Hence normalized min-sum reproduces the FP32
-// oracle bit for bit; sum-product differs only through tanhf/atanhf.
+// oracle bit for bit; sum-product differs only through expm1f/log1pf.
 #include "mbbp_internal.h"
 
 namespace mbbp {
@@ -41,6 +41,12 @@ __host__ __device__ __forceinline__ WarpLayout warp_layout(int DC, int MP, int m
     L.per_warp = L.S * 4 + L.npad * 4 + L.ehpad;
     L.hcol_bytes = align16(DC * mpad * 2);
     return L;
+}
+
+// Gallager's phi(x) = log((e^x + 1) / (e^x - 1)) = log1p(2 / expm1(x)), with
+// phi(0) = inf and phi(inf) = 0; phi is its own inverse on (0, inf).
+__device__ __forceinline__ float phi(float x) {
+    return log1pf(__fdiv_rn(2.0f, expm1f(x)));
 }
 
 // Check-node update of row r (Eq. (2) with the syndrome sign, or the
@@ -72,22 +78,27 @@ __device__ __forceinline__ void check_row(float* msg, int r, int MP, int deg, ui
             }
         }
     } else {
-        float t[DC];
+        // sum-product with Gallager's phi: |m| = phi(sum_{k != j} phi(|q_k|))
+        float f[DC];
+        uint32_t par = sbit;
 #pragma unroll
-        for (int j = 0; j < DC; ++j) t[j] = (j < deg) ? tanhf(__fmul_rn(q[j], 0.5f)) : 1.0f;
-        float pre = 1.0f;  // t_0 * ... * t_{j-1}, left to right
+        for (int j = 0; j < DC; ++j) {
+            f[j] = (j < deg) ? phi(fabsf(q[j])) : 0.0f;
+            par ^= (q[j] < 0.f) ? 1u : 0u;
+        }
+        float pre = 0.0f;  // f_0 + ... + f_{j-1}, left to right
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
             if (j < deg) {
-                float prod = pre;
+                float sum = pre;
 #pragma unroll
                 for (int k = j + 1; k < DC; ++k)
-                    if (k < deg) prod = __fmul_rn(prod, t[k]);
-                prod = fminf(fmaxf(prod, -MBBP_PMAX), MBBP_PMAX);
-                const float val = __fmul_rn(2.0f, atanhf(prod));
-                msg[j * MP + r] = sbit ? -val : val;
+                    if (k < deg) sum = __fadd_rn(sum, f[k]);
+                const float mag = fminf(phi(sum), MBBP_SP_MAX);
+                const uint32_t neg = par ^ ((q[j] < 0.f) ? 1u : 0u);
+                msg[j * MP + r] = neg ? -mag : mag;
             }
-            pre = __fmul_rn(pre, t[j]);
+            pre = __fadd_rn(pre, f[j]);
         }
     }
 }

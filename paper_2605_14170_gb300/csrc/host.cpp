@@ -176,7 +176,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
             if (set_rows[i] < 0 || set_rows[i] >= m) return fail(MBBP_E_INVALID, "set row out of range");
         maxM = std::max(maxM, m + set_ptr[t + 1] - set_ptr[t]);
     }
-    if (maxM > 1024) return fail(MBBP_E_TOO_LARGE, "a representation has more than 1024 rows");
+    if (maxM > MBBP_MAX_ROWS) return fail(MBBP_E_TOO_LARGE, "a representation has more than 1024 rows");
     // Variable degrees in every H^(t).
     int dv = 0;
     for (int t = 0; t < R; ++t) {
@@ -199,7 +199,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     mbbp_bases* B = new (std::nothrow) mbbp_bases();
     if (!B) return fail(MBBP_E_NOMEM, "host allocation failed");
     B->m = m; B->n = n; B->R = R; B->K = K; B->DV = dv; B->MP = MP; B->mpad = mpad;
-    B->W = W; B->regular = regular ? 1 : 0;
+    B->W = W; B->regular = (regular && dc == K) ? 1 : 0;  // every row fills the kernel width
     B->H.assign(H, H + (size_t)m * n);
     B->set_ptr.assign(set_ptr, set_ptr + R + 1);
     B->set_rows.assign(set_rows ? set_rows : set_ptr, set_rows ? set_rows + set_ptr[R] : set_ptr);

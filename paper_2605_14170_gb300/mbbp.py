@@ -26,7 +26,7 @@ NOISE_BSC = 0
 NOISE_DEPOLARIZING = 1
 MAX_R = 64
 LMAX = 1.0e4
-PMAX = 1.0 - 2.0 ** -23
+SP_MAX = 16.635532
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(

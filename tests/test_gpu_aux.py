@@ -72,11 +72,11 @@ def test_judge_matches_oracle(M):
             ehat[b] = (rng.random(n) < 0.05).astype(np.uint8)
         elif kind == 3:
             ehat[b, rng.integers(0, n)] ^= 1
-    # a few residuals that are logical operators
+    # a few residuals that are X-type logical operators: ker(H_Z) mod rowspace(H_X)
     L = M.mbbp_logicals_build(H, Ho)
-    ops = L.ops()
+    xops = M.mbbp_logicals_build(Ho, H).ops()
     for b in range(0, 400, 37):
-        ehat[b] = e[b] ^ ops[b % len(ops)]
+        ehat[b] = e[b] ^ xops[b % len(xops)]
     fail = torch.empty(400, dtype=torch.uint8, device="cuda")
     counts = torch.zeros(3, dtype=torch.int64, device="cuda")
     M.mbbp_judge(L, torch.from_numpy(M.pack_bits(e)).cuda(), torch.from_numpy(ehat).cuda(), fail, counts)

@@ -68,8 +68,10 @@ MUTATIONS = {
     "own edge not excluded (check)": ("bp_body.inc", "if (k == j) continue;\n                            REAL x",
                                       "REAL x"),
     "own edge not excluded (variable)": ("bp_body.inc", "if (k == i) continue;", ""),
-    "syndrome sign dropped (sum-product)": ("bp_body.inc", "c2v[j] = (st[r] & 1) ? -val : val;",
-                                            "c2v[j] = val;"),
+    "syndrome sign dropped (sum-product)": ("bp_body.inc", "REAL sum = (REAL)0;\n                        int neg = st[r] & 1;",
+                                            "REAL sum = (REAL)0;\n                        int neg = 0;"),
+    "sign of q ignored (sum-product)": ("bp_body.inc", "sum = sum + PHI(FABS(v2c[k]));\n                            if (v2c[k] < (REAL)0) neg ^= 1;",
+                                        "sum = sum + PHI(FABS(v2c[k]));"),
     "alpha not applied": ("bp_body.inc", "REAL mag = alpha * mn;", "REAL mag = mn;"),
     "eta test off by one": ("mbbp_oracle.c", "if (eta <= 1) {", "if (eta <= 2) {"),
     "FWS operands transposed": ("mbbp_oracle.c", "cnt * (best_w + 1) > best_cnt * (w + 1)",
