@@ -195,6 +195,31 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
                         uint8_t* success, int16_t* selected, float* posterior,
                         void* workspace, size_t workspace_bytes, void* stream);
 
+/* Size of the fixed device scratch behind mbbp_decode_noalloc (8 MiB). */
+#define MBBP_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+
+/* mbbp_decode for callers that cannot allocate device memory — for example a
+ * decoder embedded in a real-time control loop, where a cudaMalloc could block
+ * or fail mid-run, or a host program that links only this library and has no
+ * device allocator of its own.  The paper has no counterpart: this is a
+ * library convenience.  Arguments and outputs are those of mbbp_decode minus
+ * the workspace: the scratch lives in a fixed array of
+ * MBBP_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits.  A batch whose
+ * mbbp_decode_workspace_size exceeds it is rejected with MBBP_E_TOO_LARGE
+ * (about 26,000 shots for [[144,12,12]] with R = 16).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  The call
+ * allocates nothing and clears the part of the scratch that must start at
+ * zero.  Every call shares the one array, which keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be ordered by the caller. */
+mbbp_status mbbp_decode_noalloc(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                                const float* llr, int llr_stride, int iters, float alpha,
+                                int rule, uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run,
+                                uint8_t* success, int16_t* selected, float* posterior,
+                                void* stream);
+
 /* ------------------------------------------------------------------------
  * Logical-error judge (the logical error rate of Section IV).
  * ---------------------------------------------------------------------- */

@@ -20,12 +20,23 @@
 // over the other edges and MBBP_LMAX with a min1/min2 pair, which gives the
 // same value as the direct min.  Hence normalized min-sum reproduces the FP32
 // oracle bit for bit; sum-product differs only through expm1f/log1pf.
+#include <mutex>
+
 #include "mbbp_internal.h"
+
+// Fixed scratch for mbbp_decode_noalloc: the workspace (candidates + work
+// counter) of callers that cannot allocate device memory.  Every GPU that
+// loads this library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[mbbp::kStaticScratchBytes];
 
 namespace mbbp {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
 
 __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
 
@@ -342,6 +353,25 @@ cudaError_t launch_decode_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
 }
 
 }  // namespace
+
+cudaError_t static_scratch(void** ptr) {
+    // The array's name is a host-side stand-in in host code; the device
+    // address comes from cudaGetSymbolAddress, looked up once per device with
+    // that device current.
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *ptr = g_scratch_addr[dev];
+    return cudaSuccess;
+}
 
 size_t decode_smem_bytes(const DevBases& B, int warps) {
     const WarpLayout L = warp_layout(B.DC, B.MP, B.mpad, B.n);

@@ -496,6 +496,32 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
     return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_decode (FWS)");
 }
 
+mbbp_status mbbp_decode_noalloc(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                                const float* llr, int llr_stride, int iters, float alpha, int rule,
+                                uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run,
+                                uint8_t* success, int16_t* selected, float* posterior,
+                                void* stream) {
+    if (!B) return fail(MBBP_E_INVALID, "mbbp_decode_noalloc: NULL handle");
+    if (batch < 0) return fail(MBBP_E_INVALID, "batch must be >= 0");
+    const size_t need = mbbp_decode_workspace_size(B, batch);
+    if (need > kStaticScratchBytes) {
+        const size_t per_shot = (size_t)B->R * B->W * 4;
+        const size_t max_batch = (kStaticScratchBytes - 512) / per_shot;
+        return fail(MBBP_E_TOO_LARGE, "mbbp_decode_noalloc: batch " + std::to_string(batch) +
+                                          " needs " + std::to_string(need) +
+                                          " bytes of scratch; the fixed scratch holds " +
+                                          std::to_string(kStaticScratchBytes) +
+                                          " bytes (at most " + std::to_string(max_batch) +
+                                          " shots for this handle)");
+    }
+    void* scratch = nullptr;
+    cudaError_t e = static_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "mbbp_decode_noalloc (cudaGetSymbolAddress)");
+    return mbbp_decode(B, batch, syndromes, llr, llr_stride, iters, alpha, rule, e_hat, conv,
+                       iters_run, success, selected, posterior, scratch, kStaticScratchBytes,
+                       stream);
+}
+
 mbbp_status mbbp_logicals_build(const uint8_t* H, int m, const uint8_t* H_other, int m_other,
                                 int n, mbbp_logicals** out) {
     if (!out) return fail(MBBP_E_INVALID, "out is NULL");

@@ -11,6 +11,8 @@
 namespace mbbp {
 
 constexpr int kWarpsPerBlock = 8;
+// Size of the fixed scratch array behind mbbp_decode_noalloc.
+constexpr size_t kStaticScratchBytes = MBBP_NOALLOC_SCRATCH_BYTES;
 
 inline int words_for(int n) { return (n + 31) / 32; }
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -65,6 +67,9 @@ struct DevLogicals {
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_fws(const FwsArgs& a, cudaStream_t s);
 size_t decode_smem_bytes(const DevBases& B, int warps);
+// Device address of the fixed scratch array on the current device (looked up
+// on the first call per device).
+cudaError_t static_scratch(void** ptr);
 cudaError_t launch_sample(int n, int batch, uint64_t first_shot, uint64_t seed, uint64_t T,
                           int noise, uint32_t* ex, uint32_t* ez, cudaStream_t s);
 cudaError_t launch_syndrome(const DevBases& B, int batch, const uint32_t* e, uint8_t* synd,

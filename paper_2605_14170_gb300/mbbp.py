@@ -62,6 +62,8 @@ _sig = {
     "mbbp_decode_workspace_size": (C.c_size_t, [_vp, C.c_int]),
     "mbbp_decode": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
                               _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "mbbp_decode_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
+                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mbbp_logicals_build": (C.c_int, [_u8p, C.c_int, _u8p, C.c_int, C.c_int, C.POINTER(_vp)]),
     "mbbp_logicals_info": (C.c_int, [_vp, _vp, _vp]),
     "mbbp_judge": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
@@ -243,6 +245,24 @@ def mbbp_decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int, e
         _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
         _dptr(posterior, torch.float32, "posterior"), _dptr(workspace, torch.uint8, "workspace"),
         workspace.numel(), _stream(stream)), "mbbp_decode")
+
+
+def mbbp_decode_noalloc(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int, e_hat, conv,
+                        success, iters_run=None, selected=None, posterior=None, stream=None) -> None:
+    """mbbp_decode without a workspace, for callers that cannot allocate
+    device memory: the scratch is the library's fixed array (see mbbp.h for
+    its size limit and for why overlapping calls race)."""
+    import torch
+    batch = syndromes.shape[0]
+    if syndromes.numel() != batch * B.m:
+        raise ValueError("syndromes must be [batch, m]")
+    stride = 0 if llr.dim() == 1 else llr.shape[-1]
+    _check(_lib.mbbp_decode_noalloc(
+        B.handle, batch, _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
+        stride, iters, float(alpha), rule, _dptr(e_hat, torch.uint8, "e_hat"),
+        _dptr(conv, torch.uint8, "conv"), _dptr(iters_run, torch.int16, "iters_run"),
+        _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
+        _dptr(posterior, torch.float32, "posterior"), _stream(stream)), "mbbp_decode_noalloc")
 
 
 class Logicals:
