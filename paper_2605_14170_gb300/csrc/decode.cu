@@ -379,6 +379,7 @@ size_t decode_smem_bytes(const DevBases& B, int warps) {
 }
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count) {
+    if (a.B.shape != 0) return launch_decode_small(a, s, sm_count);
     const int K = a.B.DC;
     if (a.rule == MBBP_RULE_NMS) {
         if (K == 6) return launch_decode_t<6, MBBP_RULE_NMS>(a, s, sm_count);

@@ -155,6 +155,140 @@ mbbp_status collect_impl(const Tanner& g, int R, uint64_t seed, std::vector<int3
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Small-code layout: ELL index sigma[r] of every row r of H^(t) and the
+// variable at every position (32 positions = one warp step of the variable
+// pass).  Edge j of row r lives in shared-memory bank (sigma[r] + rot(j)) & 31.
+// In the variable pass the 32 lanes of a step read the i-th edge of their
+// variables together; the cost of that access is the largest number of lanes
+// that hit one bank.  Simulated annealing over row swaps and swaps of
+// equal-degree variables between steps lowers the summed cost; any layout
+// gives the same results, only the bank conflicts change.
+struct SmallLayout {
+    std::vector<int> sigma;  // ELL index of row r
+    std::vector<int> order;  // variable at position p
+};
+
+SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, uint64_t seed) {
+    const int M = (int)src.size();
+    constexpr int DVX = 8;
+    std::vector<std::vector<std::pair<int, int>>> ve(n);  // (row, j), ascending row
+    for (int r = 0; r < M; ++r) {
+        const auto& cols = g.rcols[src[r]];
+        for (int j = 0; j < (int)cols.size(); ++j) ve[cols[j]].push_back({r, j});
+    }
+    std::vector<std::vector<std::pair<int, int>>> re(M);  // (variable, edge index i)
+    for (int v = 0; v < n; ++v)
+        for (int i = 0; i < (int)ve[v].size(); ++i) re[ve[v][i].first].push_back({v, i});
+    SmallLayout L;
+    L.sigma.resize(M);
+    for (int r = 0; r < M; ++r) L.sigma[r] = r;
+    L.order.resize(n);
+    for (int v = 0; v < n; ++v) L.order[v] = v;
+    std::stable_sort(L.order.begin(), L.order.end(),
+                     [&](int a, int b) { return ve[a].size() < ve[b].size(); });
+    std::vector<int> posof(n);
+    for (int p = 0; p < n; ++p) posof[L.order[p]] = p;
+    const int steps = (n + 31) / 32;
+    std::vector<int> cnt((size_t)steps * DVX * 32, 0), mx((size_t)steps * DVX, 0);
+    auto bank = [&](int r, int j) { return (L.sigma[r] + slot_rot(j)) & 31; };
+    auto cell = [&](int v, int i) { return (posof[v] >> 5) * DVX + i; };
+    for (int v = 0; v < n; ++v)
+        for (int i = 0; i < (int)ve[v].size(); ++i) ++cnt[(size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second)];
+    auto remax = [&](int c) {
+        int x = 0;
+        for (int k = 0; k < 32; ++k) x = std::max(x, cnt[(size_t)c * 32 + k]);
+        mx[c] = x;
+    };
+    long total = 0;
+    for (int c = 0; c < steps * DVX; ++c) { remax(c); total += mx[c]; }
+    std::vector<int> best_sigma = L.sigma, best_order = L.order;
+    long best = total;
+    uint64_t rs = seed;
+    auto rnd = [&]() { rs += 0x9E3779B97F4A7C15ULL; uint64_t z = rs;
+                       z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+                       z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL; return z ^ (z >> 31); };
+    std::vector<int> cells;
+    const int iters = 12000;
+    for (int it = 0; it < iters; ++it) {
+        const double T = 0.6 * (1.0 - (double)it / iters) + 0.02;
+        cells.clear();
+        long before = 0, after = 0;
+        const bool row_move = (rnd() & 1) || steps == 1;
+        int a = 0, b = 0;
+        if (row_move) {
+            a = (int)(rnd() % M);
+            b = (int)(rnd() % M);
+            if (a == b) continue;
+            for (int rr : {a, b})
+                for (auto& e : re[rr]) cells.push_back(cell(e.first, e.second));
+            std::sort(cells.begin(), cells.end());
+            cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
+            for (int c : cells) before += mx[c];
+            const std::vector<int> keep = cells;
+            for (int rr : {a, b})
+                for (auto& e : re[rr]) --cnt[(size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second)];
+            std::swap(L.sigma[a], L.sigma[b]);
+            for (int rr : {a, b})
+                for (auto& e : re[rr]) ++cnt[(size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second)];
+            for (int c : keep) { remax(c); after += mx[c]; }
+            const long d = after - before;
+            const double u = (double)(rnd() >> 11) * (1.0 / 9007199254740992.0);
+            if (d <= 0 || u < std::exp(-(double)d / T)) {
+                total += d;
+            } else {
+                for (int rr : {a, b})
+                    for (auto& e : re[rr]) --cnt[(size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second)];
+                std::swap(L.sigma[a], L.sigma[b]);
+                for (int rr : {a, b})
+                    for (auto& e : re[rr]) ++cnt[(size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second)];
+                for (int c : keep) remax(c);
+            }
+        } else {
+            const int pa = (int)(rnd() % n), pb = (int)(rnd() % n);
+            const int va = L.order[pa], vb = L.order[pb];
+            if ((pa >> 5) == (pb >> 5) || ve[va].size() != ve[vb].size()) continue;
+            for (int v : {va, vb})
+                for (int i = 0; i < (int)ve[v].size(); ++i) cells.push_back(cell(v, i));
+            for (int i = 0; i < (int)ve[va].size(); ++i) {
+                cells.push_back((pb >> 5) * DVX + i);
+                cells.push_back((pa >> 5) * DVX + i);
+            }
+            std::sort(cells.begin(), cells.end());
+            cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
+            for (int c : cells) before += mx[c];
+            const std::vector<int> keep = cells;
+            auto swap_vars = [&]() {
+                for (int v : {va, vb})
+                    for (int i = 0; i < (int)ve[v].size(); ++i)
+                        --cnt[(size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second)];
+                std::swap(L.order[posof[va]], L.order[posof[vb]]);
+                std::swap(posof[va], posof[vb]);
+                for (int v : {va, vb})
+                    for (int i = 0; i < (int)ve[v].size(); ++i)
+                        ++cnt[(size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second)];
+            };
+            swap_vars();
+            for (int c : keep) { remax(c); after += mx[c]; }
+            const long d = after - before;
+            const double u = (double)(rnd() >> 11) * (1.0 / 9007199254740992.0);
+            if (d <= 0 || u < std::exp(-(double)d / T)) {
+                total += d;
+            } else {
+                swap_vars();
+                for (int c : keep) remax(c);
+            }
+        }
+        if (total < best) {
+            best = total;
+            best_sigma = L.sigma;
+            best_order = L.order;
+        }
+    }
+    L.sigma = best_sigma;
+    L.order = best_order;
+    return L;
+}
+
 mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set_ptr,
                        const int32_t* set_rows, mbbp_bases** out) {
     if (!out) return fail(MBBP_E_INVALID, "out is NULL");
@@ -235,6 +369,64 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
             vslot.insert(vslot.end(), vl[v].begin(), vl[v].end());
         }
     }
+    // Small-code tables (register-resident kernel), when a shape fits.
+    int shape = 0;
+    if (K == 6)
+        for (int i = 0; i < kNumSmallShapes && !shape; ++i)
+            if (n <= 32 * kSmallShapes[i].VS && MP <= 32 * kSmallShapes[i].RS &&
+                m <= 32 * kSmallShapes[i].ORS)
+                shape = i + 1;
+    std::vector<uint4> vdesc2;
+    std::vector<uint32_t> rinfo2, hmask2;
+    int VS = 0, RS = 0, ORS = 0;
+    if (shape) {
+        VS = kSmallShapes[shape - 1].VS;
+        RS = kSmallShapes[shape - 1].RS;
+        ORS = kSmallShapes[shape - 1].ORS;
+        vdesc2.assign((size_t)R * VS * 32, make_uint4(0, 0, 0, 0));
+        rinfo2.assign((size_t)R * MP, 0);
+        hmask2.assign((size_t)R * VS * ORS * 32, 0);
+        for (int t = 0; t < R; ++t) {
+            const int extra = set_ptr[t + 1] - set_ptr[t];
+            std::vector<int> src(m + extra);
+            for (int r = 0; r < m + extra; ++r) src[r] = r < m ? r : set_rows[set_ptr[t] + (r - m)];
+            const SmallLayout L = small_layout(g, src, n, 0x5EEDull + (uint64_t)t);
+            std::vector<int> posof(n);
+            for (int p = 0; p < n; ++p) posof[L.order[p]] = p;
+            std::vector<std::vector<uint16_t>> vs(n);
+            for (int r = 0; r < (int)src.size(); ++r) {
+                const auto& cols = g.rcols[src[r]];
+                const int sg = L.sigma[r];
+                rinfo2[(size_t)t * MP + sg] = (uint32_t)src[r] | ((uint32_t)cols.size() << 16);
+                for (int j = 0; j < (int)cols.size(); ++j)
+                    vs[cols[j]].push_back((uint16_t)(j * MP + (sg & ~31) + ((sg + slot_rot(j)) & 31)));
+            }
+            // byte offsets within a warp's message area; a missing edge (and
+            // every edge of a padding position) points at the zero slot
+            const uint16_t zero_slot = (uint16_t)(4 * 6 * MP);
+            for (int p = n; p < VS * 32; ++p) {
+                const uint32_t z = zero_slot | ((uint32_t)zero_slot << 16);
+                vdesc2[(size_t)t * VS * 32 + p] = make_uint4(0, z, z, z);
+            }
+            for (int p = 0; p < n; ++p) {
+                const int v = L.order[p];
+                uint16_t sl[6] = {zero_slot, zero_slot, zero_slot, zero_slot, zero_slot, zero_slot};
+                for (int i = 0; i < (int)vs[v].size(); ++i) sl[i] = (uint16_t)(4 * vs[v][i]);
+                uint4 d;
+                d.x = (uint32_t)v | ((uint32_t)vs[v].size() << 16);
+                d.y = sl[0] | ((uint32_t)sl[1] << 16);
+                d.z = sl[2] | ((uint32_t)sl[3] << 16);
+                d.w = sl[4] | ((uint32_t)sl[5] << 16);
+                vdesc2[(size_t)t * VS * 32 + p] = d;
+            }
+            for (int r = 0; r < m; ++r)
+                for (int c : g.rcols[r]) {
+                    const int pp = posof[c];
+                    hmask2[((size_t)t * VS + (pp >> 5)) * (ORS * 32) + r] |= 1u << (pp & 31);
+                }
+        }
+    }
+
     std::vector<uint16_t> hcol((size_t)K * mpad, (uint16_t)n);
     std::vector<uint32_t> hmask((size_t)m * W, 0);
     for (int r = 0; r < m; ++r)
@@ -253,7 +445,10 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     const size_t o_rows = o_vslot + align256(std::max<size_t>(vslot.size(), 1) * 2);
     const size_t o_hcol = o_rows + align256(rows.size() * 4);
     const size_t o_hmask = o_hcol + align256(hcol.size() * 2);
-    const size_t total = o_hmask + align256(hmask.size() * 4);
+    const size_t o_vdesc2 = o_hmask + align256(hmask.size() * 4);
+    const size_t o_rinfo2 = o_vdesc2 + align256(vdesc2.size() * sizeof(uint4));
+    const size_t o_hmask2 = o_rinfo2 + align256(rinfo2.size() * 4);
+    const size_t total = o_hmask2 + align256(hmask2.size() * 4);
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
     if (e == cudaSuccess) e = cudaMalloc(&B->dmem, total);
@@ -269,6 +464,9 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         {o_rows, rows.data(), rows.size() * 4},
         {o_hcol, hcol.data(), hcol.size() * 2},
         {o_hmask, hmask.data(), hmask.size() * 4},
+        {o_vdesc2, vdesc2.data(), vdesc2.size() * sizeof(uint4)},
+        {o_rinfo2, rinfo2.data(), rinfo2.size() * 4},
+        {o_hmask2, hmask2.data(), hmask2.size() * 4},
     };
     for (const Copy& c : copies) {
         if (c.bytes == 0) continue;
@@ -288,6 +486,13 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     d.hmask = reinterpret_cast<const uint32_t*>(base + o_hmask);
     d.m = m; d.n = n; d.R = R; d.DC = K; d.DV = dv; d.MP = MP; d.mpad = mpad; d.W = W;
     d.regular = B->regular;
+    d.shape = shape;
+    d.VS = VS;
+    d.RS = RS;
+    d.ORS = ORS;
+    d.vdesc2 = shape ? reinterpret_cast<const uint4*>(base + o_vdesc2) : nullptr;
+    d.rinfo2 = shape ? reinterpret_cast<const uint32_t*>(base + o_rinfo2) : nullptr;
+    d.hmask2 = shape ? reinterpret_cast<const uint32_t*>(base + o_hmask2) : nullptr;
     *out = B;
     return MBBP_OK;
 }

@@ -31,7 +31,25 @@ struct DevBases {
     const uint32_t* hmask;    // [m][W] rows of H as bit masks
     int m, n, R, DC, DV, MP, mpad, W;
     int regular;              // every row of H has weight DC
+
+    // Small-code layout (shape != 0; K = 6 and n <= 32 VS): rows placed at
+    // ELL index sigma(r), edge j of the row at slot
+    // j*MP + (sigma(r) & ~31) + ((sigma(r) + rot(j)) & 31), chosen by the host
+    // to spread the variable pass over the shared-memory banks.
+    const uint4* vdesc2;      // [R][VS*32] x = variable | degree << 16, y/z/w = 6 slot ids (u16)
+    const uint32_t* rinfo2;   // [R][MP] ELL index -> src row | degree << 16
+    const uint32_t* hmask2;   // [R][VS][ORS*32] rows of H as bit masks over positions
+    int shape, VS, RS, ORS;
 };
+
+// Bank rotation of edge position j in the small-code layout.
+__host__ __device__ constexpr int slot_rot(int j) { return (j * 11) & 31; }
+
+struct SmallShape {
+    int VS, RS, ORS;  // variable steps, row steps of H^(t), row steps of H (32 lanes each)
+};
+constexpr SmallShape kSmallShapes[] = {{3, 2, 2}, {5, 3, 3}, {5, 4, 3}};
+constexpr int kNumSmallShapes = 3;
 
 struct DecodeArgs {
     DevBases B;
@@ -63,8 +81,9 @@ struct DevLogicals {
     int m, n, k, DC, mpad, W;
 };
 
-// Launchers (decode.cu, aux.cu).  They return cudaGetLastError().
+// Launchers (decode.cu, decode_small.cu, aux.cu).  They return cudaGetLastError().
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_decode_small(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_fws(const FwsArgs& a, cudaStream_t s);
 size_t decode_smem_bytes(const DevBases& B, int warps);
 // Device address of the fixed scratch array on the current device (looked up
