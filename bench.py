@@ -40,6 +40,9 @@ ITERS = 100
 ALPHA = 0.625
 SEED = 20260515
 OPS_PER_EDGE_UPDATE = 10  # algorithmic ALU operations per edge-update (min-sum flooding)
+# DRAM bytes per shot of the BP kernel (ncu capture of a 100k-shot launch:
+# 7.33 MB read + 2.6 KB written); None once the kernel changes
+DRAM_BYTES_PER_SHOT = (7.33e6 + 2.6e3) / 100000
 WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
 
 
@@ -325,7 +328,11 @@ def main():
             "decoded_syndromes_per_s": 2 * value,
             "ler": ler,
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                         "unit": "Tops/s", "frac": achieved_ops / peak_ops,
+                         "traffic": DRAM_BYTES_PER_SHOT * S,
+                         "traffic_note": "dram read+write of the BP kernel from one ncu capture of a "
+                                         "100k-shot launch (profiles/decode_small_kernel_bb144_r16.md), "
+                                         "scaled by shots",
                          "kernel": "mbbp_decode (BP + FWS)", "decode_ms_avg": dec_avg_ms,
                          "edge_updates_per_launch": edge_per_launch,
                          "ops_per_edge_update": OPS_PER_EDGE_UPDATE,
