@@ -195,6 +195,63 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
                         uint8_t* success, int16_t* selected, float* posterior,
                         void* workspace, size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Mixed batches: several codes decoded by one persistent launch.
+ * ---------------------------------------------------------------------- */
+
+/* A plan for decoding the shots of up to 8 codes together (Algorithm 1 for
+ * each code's shots, as mbbp_decode).  The plan keeps the code handles
+ * (which must outlive it) and its launch configuration: warps per block,
+ * shots per work item and kernel path per code, and the order of the codes
+ * in the work list (heaviest first by default). */
+typedef struct mbbp_plan mbbp_plan;
+
+/* Inputs and outputs of one code in a mixed batch; the meaning, layout and
+ * optionality of every field are those of the mbbp_decode argument of the
+ * same name (device pointers; llr_stride 0 = one LLR vector for all shots). */
+typedef struct {
+    int batch;
+    const uint8_t* syndromes;
+    const float* llr;
+    int llr_stride;
+    uint8_t* e_hat;
+    uint8_t* conv;
+    uint16_t* iters_run;
+    uint8_t* success;
+    int16_t* selected;
+} mbbp_code_io;
+
+mbbp_status mbbp_plan_create(const mbbp_bases* const* codes, int n_codes, mbbp_plan** out);
+void mbbp_plan_free(mbbp_plan* P);
+
+/* Workspace bytes for the given per-code batches (host int32[n_codes]). */
+size_t mbbp_plan_workspace_size(const mbbp_plan* P, const int32_t* batches);
+
+/* Decode io[c] (host array of n_codes entries) with code c of the plan: one
+ * persistent BP launch over every (code, shot chunk, representation) work
+ * item, then FWS per code.  Outputs are identical to one mbbp_decode per
+ * code.  Only kernel launches and a memset are enqueued, so the call can be
+ * captured into a CUDA graph (after the first call with the same plan, shapes
+ * and block size, which sets kernel attributes).  Workspace: as mbbp_decode,
+ * its first region holds each code's candidates in code order. */
+mbbp_status mbbp_decode_mixed(const mbbp_plan* P, const mbbp_code_io* io, int iters, float alpha,
+                              int rule, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Choose the plan's launch configuration by timing mbbp_decode_mixed on the
+ * given inputs (coordinate descent over warps per block in {4, 8}, shots per
+ * work item in {1, 2, 4, 8, 16} and the kernel path per code, then the code
+ * order).  Synchronises the stream, overwrites the outputs; not capturable.
+ * best_ms: host float or NULL, the time of the chosen configuration. */
+mbbp_status mbbp_plan_autotune(mbbp_plan* P, const mbbp_code_io* io, int iters, float alpha,
+                               int rule, void* workspace, size_t workspace_bytes, void* stream,
+                               float* best_ms);
+
+/* The plan's configuration: warps per block; per code (host int32[n_codes]
+ * each, or NULL) shots per work item, path (0 small-code, 1 generic) and the
+ * work-list order. */
+mbbp_status mbbp_plan_info(const mbbp_plan* P, int32_t* warps, int32_t* chunk, int32_t* kind,
+                           int32_t* order);
+
 /* Size of the fixed device scratch behind mbbp_decode_noalloc (8 MiB). */
 #define MBBP_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 

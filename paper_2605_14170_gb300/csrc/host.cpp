@@ -24,6 +24,15 @@ struct mbbp_bases {
     DevBases dev{};
 };
 
+struct mbbp_plan {
+    std::vector<const mbbp_bases*> codes;
+    int device = 0, sm_count = 0;
+    int warps = 8;               // warps per block of the persistent kernel
+    std::vector<int> chunk;      // shots per work item, per code
+    std::vector<int> kind;       // kKindSmall / kKindGeneric, per code
+    std::vector<int> order;      // codes in work-list order
+};
+
 struct mbbp_logicals {
     int m = 0, n = 0, k = 0, K = 0, mpad = 0, W = 0, device = 0;
     std::vector<uint8_t> ops;  // k x n
@@ -670,25 +679,25 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
     cudaStream_t s = (cudaStream_t)stream;
     DecodeArgs a{};
     a.B = B->dev;
-    a.synd = syndromes;
-    a.llr = llr;
-    a.llr_stride = llr_stride;
-    a.batch = batch;
-    a.iters = iters;
+    a.io.synd = syndromes;
+    a.io.llr = llr;
+    a.io.llr_stride = llr_stride;
+    a.io.batch = batch;
+    a.io.iters = iters;
+    a.io.alpha = alpha;
     a.rule = rule;
-    a.alpha = alpha;
     const size_t cand_bytes = align256((size_t)batch * B->R * B->W * 4);
-    a.cand = static_cast<uint32_t*>(workspace);
+    a.io.cand = static_cast<uint32_t*>(workspace);
     a.counter = reinterpret_cast<unsigned long long*>(static_cast<char*>(workspace) + cand_bytes);
-    a.conv = conv;
-    a.iters_run = iters_run;
-    a.post = posterior;
+    a.io.conv = conv;
+    a.io.iters_run = iters_run;
+    a.io.post = posterior;
     a.total_items = (unsigned long long)batch * B->R;
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = launch_decode(a, s, B->sm_count);
     if (e != cudaSuccess) return cuda_fail(e, "mbbp_decode (BP)");
     FwsArgs f{};
-    f.cand = a.cand;
+    f.cand = a.io.cand;
     f.conv = conv;
     f.batch = batch;
     f.R = B->R;
@@ -725,6 +734,220 @@ mbbp_status mbbp_decode_noalloc(const mbbp_bases* B, int batch, const uint8_t* s
     return mbbp_decode(B, batch, syndromes, llr, llr_stride, iters, alpha, rule, e_hat, conv,
                        iters_run, success, selected, posterior, scratch, kStaticScratchBytes,
                        stream);
+}
+
+// ------------------------------------------------------------ mixed batches
+
+mbbp_status mbbp_plan_create(const mbbp_bases* const* codes, int n_codes, mbbp_plan** out) {
+    if (!out) return fail(MBBP_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!codes || n_codes < 1 || n_codes > kMixedMaxCodes)
+        return fail(MBBP_E_INVALID, "n_codes must be in [1, 8]");
+    int dev = -1;
+    for (int c = 0; c < n_codes; ++c) {
+        if (!codes[c]) return fail(MBBP_E_INVALID, "NULL code handle");
+        if (c > 0 && codes[c]->device != dev) return fail(MBBP_E_INVALID, "codes on different devices");
+        dev = codes[c]->device;
+    }
+    mbbp_plan* P = new (std::nothrow) mbbp_plan();
+    if (!P) return fail(MBBP_E_NOMEM, "host allocation failed");
+    P->codes.assign(codes, codes + n_codes);
+    P->device = dev;
+    P->sm_count = codes[0]->sm_count;
+    P->chunk.assign(n_codes, 4);
+    P->kind.resize(n_codes);
+    for (int c = 0; c < n_codes; ++c)
+        P->kind[c] = (codes[c]->dev.shape != 0 && codes[c]->regular) ? kKindSmall : kKindGeneric;
+    // heaviest codes first: work = R * edges per representation
+    std::vector<double> cost(n_codes);
+    for (int c = 0; c < n_codes; ++c) {
+        double e = 0;
+        for (int t = 0; t < codes[c]->R; ++t) e += codes[c]->edges[t];
+        cost[c] = e;
+    }
+    P->order.resize(n_codes);
+    for (int c = 0; c < n_codes; ++c) P->order[c] = c;
+    std::stable_sort(P->order.begin(), P->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    *out = P;
+    return MBBP_OK;
+}
+
+void mbbp_plan_free(mbbp_plan* P) { delete P; }
+
+size_t mbbp_plan_workspace_size(const mbbp_plan* P, const int32_t* batches) {
+    if (!P || !batches) return 0;
+    size_t total = 256;  // work counter
+    for (size_t c = 0; c < P->codes.size(); ++c) {
+        if (batches[c] < 0) return 0;
+        total += align256((size_t)batches[c] * P->codes[c]->R * P->codes[c]->W * 4);
+    }
+    return total;
+}
+
+mbbp_status mbbp_plan_info(const mbbp_plan* P, int32_t* warps, int32_t* chunk, int32_t* kind,
+                           int32_t* order) {
+    if (!P) return fail(MBBP_E_INVALID, "mbbp_plan_info: NULL plan");
+    if (warps) *warps = P->warps;
+    for (size_t c = 0; c < P->codes.size(); ++c) {
+        if (chunk) chunk[c] = P->chunk[c];
+        if (kind) kind[c] = P->kind[c];
+        if (order) order[c] = P->order[c];
+    }
+    return MBBP_OK;
+}
+
+namespace {
+
+mbbp_status mixed_impl(const mbbp_plan* P, const mbbp_code_io* io, int iters, float alpha, int rule,
+                       void* workspace, size_t workspace_bytes, cudaStream_t s) {
+    const int nc = (int)P->codes.size();
+    if (!io) return fail(MBBP_E_INVALID, "io is NULL");
+    if (iters < 0 || iters > MBBP_MAX_ITERS) return fail(MBBP_E_INVALID, "iters out of range");
+    if (rule != MBBP_RULE_NMS && rule != MBBP_RULE_SP) return fail(MBBP_E_INVALID, "unknown rule");
+    if (rule == MBBP_RULE_NMS && !(alpha > 0.f && alpha <= 1.f))
+        return fail(MBBP_E_INVALID, "alpha must be in (0, 1]");
+    std::vector<int32_t> batches(nc);
+    for (int c = 0; c < nc; ++c) {
+        const mbbp_code_io& x = io[c];
+        const mbbp_bases* B = P->codes[c];
+        if (x.batch < 0) return fail(MBBP_E_INVALID, "batch must be >= 0");
+        if (x.batch > 0 && (!x.syndromes || !x.llr || !x.e_hat || !x.conv || !x.success))
+            return fail(MBBP_E_INVALID, "mbbp_decode_mixed: NULL buffer");
+        if (x.llr_stride != 0 && x.llr_stride < B->n) return fail(MBBP_E_INVALID, "llr_stride must be 0 or >= n");
+        batches[c] = x.batch;
+    }
+    if (!workspace || workspace_bytes < mbbp_plan_workspace_size(P, batches.data()))
+        return fail(MBBP_E_INVALID, "workspace too small");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(MBBP_E_INVALID, "workspace must be 256-byte aligned");
+    if (mbbp_status st = check_device(P->device)) return st;
+    MixedArgs a{};
+    char* ws = static_cast<char*>(workspace);
+    std::vector<uint32_t*> cand(nc);
+    for (int c = 0; c < nc; ++c) {
+        cand[c] = reinterpret_cast<uint32_t*>(ws);
+        ws += align256((size_t)batches[c] * P->codes[c]->R * P->codes[c]->W * 4);
+    }
+    a.counter = reinterpret_cast<unsigned long long*>(ws);
+    unsigned long long first = 0;
+    size_t warp_bytes = 16;
+    int slot = 0;
+    for (int oi = 0; oi < nc; ++oi) {
+        const int c = P->order[oi];
+        const mbbp_bases* B = P->codes[c];
+        const mbbp_code_io& x = io[c];
+        if (x.batch == 0) continue;
+        MixedCode& mc = a.codes[slot++];
+        mc.B = B->dev;
+        mc.kind = P->kind[c];
+        mc.chunk = P->chunk[c];
+        mc.io.synd = x.syndromes;
+        mc.io.llr = x.llr;
+        mc.io.llr_stride = x.llr_stride;
+        mc.io.batch = x.batch;
+        mc.io.iters = iters;
+        mc.io.alpha = alpha;
+        mc.io.cand = cand[c];
+        mc.io.conv = x.conv;
+        mc.io.iters_run = x.iters_run;
+        mc.io.post = nullptr;
+        mc.first = first;
+        first += (unsigned long long)((x.batch + mc.chunk - 1) / mc.chunk) * B->R;
+        warp_bytes = std::max(warp_bytes, mixed_warp_bytes(B->dev, mc.kind));
+    }
+    a.n_codes = slot;
+    a.total = first;
+    a.warp_bytes = (uint32_t)((warp_bytes + 15) & ~(size_t)15);
+    if ((size_t)P->warps * a.warp_bytes > 200 * 1024) return fail(MBBP_E_TOO_LARGE, "shared memory per block");
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess && a.total > 0) e = launch_mixed(a, P->warps, rule, s, P->sm_count);
+    if (e != cudaSuccess) return cuda_fail(e, "mbbp_decode_mixed (BP)");
+    for (int c = 0; c < nc; ++c) {
+        const mbbp_code_io& x = io[c];
+        if (x.batch == 0) continue;
+        FwsArgs f{};
+        f.cand = cand[c];
+        f.conv = x.conv;
+        f.batch = x.batch;
+        f.R = P->codes[c]->R;
+        f.n = P->codes[c]->n;
+        f.W = P->codes[c]->W;
+        f.e_hat = x.e_hat;
+        f.success = x.success;
+        f.selected = x.selected;
+        e = launch_fws(f, s);
+        if (e != cudaSuccess) return cuda_fail(e, "mbbp_decode_mixed (FWS)");
+    }
+    return MBBP_OK;
+}
+
+}  // namespace
+
+mbbp_status mbbp_decode_mixed(const mbbp_plan* P, const mbbp_code_io* io, int iters, float alpha,
+                              int rule, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!P) return fail(MBBP_E_INVALID, "mbbp_decode_mixed: NULL plan");
+    return mixed_impl(P, io, iters, alpha, rule, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+mbbp_status mbbp_plan_autotune(mbbp_plan* P, const mbbp_code_io* io, int iters, float alpha, int rule,
+                               void* workspace, size_t workspace_bytes, void* stream, float* best_ms) {
+    if (!P) return fail(MBBP_E_INVALID, "mbbp_plan_autotune: NULL plan");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err != cudaSuccess) return cuda_fail(err, "mbbp_plan_autotune");
+    // time one configuration: one untimed run, then the best of two
+    auto measure = [&](float* ms) -> mbbp_status {
+        if (mbbp_status st = mixed_impl(P, io, iters, alpha, rule, workspace, workspace_bytes, s)) return st;
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, s);
+            if (mbbp_status st = mixed_impl(P, io, iters, alpha, rule, workspace, workspace_bytes, s)) return st;
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) return cuda_fail(e, "mbbp_plan_autotune");
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, t);
+        }
+        *ms = best;
+        return MBBP_OK;
+    };
+    float best = 0;
+    mbbp_status st = measure(&best);
+    const int nc = (int)P->codes.size();
+    // coordinate descent over: block size, per-code chunk, per-code path, order
+    auto try_value = [&](int* knob, int value) -> mbbp_status {
+        const int old = *knob;
+        if (old == value) return MBBP_OK;
+        *knob = value;
+        float t = 0;
+        mbbp_status r = measure(&t);
+        if (r != MBBP_OK) { *knob = old; return r; }
+        if (t < best) best = t;
+        else *knob = old;
+        return MBBP_OK;
+    };
+    for (int w : {4, 8}) if (st == MBBP_OK) st = try_value(&P->warps, w);
+    for (int c = 0; c < nc && st == MBBP_OK; ++c) {
+        for (int ch : {1, 2, 4, 8, 16}) if (st == MBBP_OK) st = try_value(&P->chunk[c], ch);
+        if (st == MBBP_OK && P->codes[c]->dev.shape != 0 && P->codes[c]->regular)
+            st = try_value(&P->kind[c], P->kind[c] == kKindSmall ? kKindGeneric : kKindSmall);
+    }
+    if (st == MBBP_OK && nc > 1) {
+        std::vector<int> old = P->order;
+        std::reverse(P->order.begin(), P->order.end());
+        float t = 0;
+        st = measure(&t);
+        if (st == MBBP_OK && t < best) best = t;
+        else P->order = old;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MBBP_OK) return st;
+    if (best_ms) *best_ms = best;
+    return MBBP_OK;
 }
 
 mbbp_status mbbp_logicals_build(const uint8_t* H, int m, const uint8_t* H_other, int m_other,

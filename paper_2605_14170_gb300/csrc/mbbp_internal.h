@@ -51,17 +51,23 @@ struct SmallShape {
 constexpr SmallShape kSmallShapes[] = {{3, 2, 2}, {5, 3, 3}, {5, 4, 3}};
 constexpr int kNumSmallShapes = 3;
 
-struct DecodeArgs {
-    DevBases B;
+// Inputs and per-representation outputs of one code's batch of shots.
+struct ShotIO {
     const uint8_t* synd;      // [batch][m]
     const float* llr;         // [n] or [batch][llr_stride]
     int llr_stride;
-    int batch, iters, rule;
+    int batch, iters;
     float alpha;
     uint32_t* cand;           // [batch][R][W]
     uint8_t* conv;            // [batch][R]
     uint16_t* iters_run;      // [batch][R] or null
     float* post;              // [batch][R][n] or null
+};
+
+struct DecodeArgs {
+    DevBases B;
+    ShotIO io;
+    int rule;
     unsigned long long* counter;
     unsigned long long total_items;
 };
@@ -81,6 +87,28 @@ struct DevLogicals {
     int m, n, k, DC, mpad, W;
 };
 
+// One code of a mixed batch (decode_mixed.cu).
+constexpr int kMixedMaxCodes = 8;
+constexpr int kMixedMaxWarps = 8;
+constexpr int kKindSmall = 0;    // register-resident small-code path
+constexpr int kKindGeneric = 1;  // generic path
+struct MixedCode {
+    DevBases B;
+    ShotIO io;
+    int kind;                   // kKindSmall / kKindGeneric
+    int chunk;                  // shots per work item
+    unsigned long long first;   // first global work index of this code
+};
+struct MixedArgs {
+    MixedCode codes[kMixedMaxCodes];
+    int n_codes;
+    uint32_t warp_bytes;        // shared memory per warp (largest over codes)
+    unsigned long long total;   // work items
+    unsigned long long* counter;
+};
+size_t mixed_warp_bytes(const DevBases& B, int kind);
+cudaError_t launch_mixed(const MixedArgs& a, int warps, int rule, cudaStream_t s, int sm_count);
+
 // Launchers (decode.cu, decode_small.cu, aux.cu).  They return cudaGetLastError().
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_decode_small(const DecodeArgs& a, cudaStream_t s, int sm_count);
@@ -89,6 +117,9 @@ size_t decode_smem_bytes(const DevBases& B, int warps);
 // Device address of the fixed scratch array on the current device (looked up
 // on the first call per device).
 cudaError_t static_scratch(void** ptr);
+// Sets the dynamic shared-memory limit of a kernel and returns its blocks per
+// SM, once per (kernel, block size, shared memory, device); cached afterwards.
+cudaError_t prepare_kernel(const void* func, int threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_sample(int n, int batch, uint64_t first_shot, uint64_t seed, uint64_t T,
                           int noise, uint32_t* ex, uint32_t* ez, cudaStream_t s);
 cudaError_t launch_syndrome(const DevBases& B, int batch, const uint32_t* e, uint8_t* synd,

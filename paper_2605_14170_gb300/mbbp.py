@@ -42,6 +42,13 @@ class MBBPError(RuntimeError):
         self.status = status
 
 
+class CodeIO(C.Structure):
+    """mbbp_code_io: one code's device buffers in a mixed batch."""
+    _fields_ = [("batch", C.c_int), ("syndromes", C.c_void_p), ("llr", C.c_void_p),
+                ("llr_stride", C.c_int), ("e_hat", C.c_void_p), ("conv", C.c_void_p),
+                ("iters_run", C.c_void_p), ("success", C.c_void_p), ("selected", C.c_void_p)]
+
+
 _i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
 _u8p = np.ctypeslib.ndpointer(np.uint8, flags="C")
 _vp = C.c_void_p
@@ -64,6 +71,14 @@ _sig = {
                               _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_decode_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
                                       _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mbbp_plan_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
+    "mbbp_plan_free": (None, [_vp]),
+    "mbbp_plan_workspace_size": (C.c_size_t, [_vp, _i32p]),
+    "mbbp_decode_mixed": (C.c_int, [_vp, C.POINTER(CodeIO), C.c_int, C.c_float, C.c_int, _vp,
+                                    C.c_size_t, _vp]),
+    "mbbp_plan_autotune": (C.c_int, [_vp, C.POINTER(CodeIO), C.c_int, C.c_float, C.c_int, _vp,
+                                     C.c_size_t, _vp, C.POINTER(C.c_float)]),
+    "mbbp_plan_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "mbbp_logicals_build": (C.c_int, [_u8p, C.c_int, _u8p, C.c_int, C.c_int, C.POINTER(_vp)]),
     "mbbp_logicals_info": (C.c_int, [_vp, _vp, _vp]),
     "mbbp_judge": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
@@ -263,6 +278,91 @@ def mbbp_decode_noalloc(B: Bases, syndromes, llr, iters: int, alpha: float, rule
         _dptr(conv, torch.uint8, "conv"), _dptr(iters_run, torch.int16, "iters_run"),
         _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
         _dptr(posterior, torch.float32, "posterior"), _stream(stream)), "mbbp_decode_noalloc")
+
+
+class Plan:
+    """Owner of an ``mbbp_plan`` (keeps its code handles alive)."""
+
+    def __init__(self, codes):
+        self.codes = list(codes)
+        arr = (C.c_void_p * len(self.codes))(*[c.handle.value for c in self.codes])
+        out = C.c_void_p()
+        _check(_lib.mbbp_plan_create(arr, len(self.codes), C.byref(out)), "mbbp_plan_create")
+        self.handle = out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.mbbp_plan_free(h)
+            self.handle = C.c_void_p(None)
+
+
+def mbbp_plan_create(codes) -> Plan:
+    return Plan(codes)
+
+
+def mbbp_plan_workspace_size(P: Plan, batches) -> int:
+    return int(_lib.mbbp_plan_workspace_size(P.handle, np.ascontiguousarray(batches, dtype=np.int32)))
+
+
+def mbbp_plan_info(P: Plan) -> dict:
+    nc = len(P.codes)
+    warps = C.c_int32()
+    chunk, kind, order = (np.zeros(nc, np.int32) for _ in range(3))
+    _check(_lib.mbbp_plan_info(P.handle, C.cast(C.pointer(warps), _vp), _np_ptr(chunk), _np_ptr(kind),
+                               _np_ptr(order)), "mbbp_plan_info")
+    return {"warps": warps.value, "chunk": chunk.tolist(), "kind": kind.tolist(), "order": order.tolist()}
+
+
+def _code_io(ios):
+    import torch
+    arr = (CodeIO * len(ios))()
+    for i, x in enumerate(ios):
+        batch = x["syndromes"].shape[0]
+        llr = x["llr"]
+        arr[i] = CodeIO(batch, _dptr(x["syndromes"], torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
+                        0 if llr.dim() == 1 else llr.shape[-1], _dptr(x["e_hat"], torch.uint8, "e_hat"),
+                        _dptr(x["conv"], torch.uint8, "conv"), _dptr(x.get("iters"), torch.int16, "iters"),
+                        _dptr(x["success"], torch.uint8, "success"), _dptr(x.get("selected"), torch.int16, "selected"))
+    return arr
+
+
+def mbbp_decode_mixed(P: Plan, ios, iters: int, alpha: float, rule: int, workspace, stream=None) -> None:
+    """ios: one dict per code of the plan with CUDA tensors syndromes, llr,
+    e_hat, conv, success and optionally iters (int16) and selected."""
+    import torch
+    arr = _code_io(ios)
+    _check(_lib.mbbp_decode_mixed(P.handle, arr, iters, float(alpha), rule,
+                                  _dptr(workspace, torch.uint8, "workspace"), workspace.numel(), _stream(stream)),
+           "mbbp_decode_mixed")
+
+
+def mbbp_plan_autotune(P: Plan, ios, iters: int, alpha: float, rule: int, workspace, stream=None) -> float:
+    import torch
+    arr = _code_io(ios)
+    best = C.c_float(0.0)
+    _check(_lib.mbbp_plan_autotune(P.handle, arr, iters, float(alpha), rule,
+                                   _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
+                                   _stream(stream), C.byref(best)), "mbbp_plan_autotune")
+    return best.value
+
+
+def mixed_buffers(P: Plan, syndromes, llrs) -> tuple[list, object]:
+    """Allocate per-code outputs (torch, on the syndromes' device) and the
+    workspace for mbbp_decode_mixed; returns (ios, workspace)."""
+    import torch
+    ios = []
+    for B, s, l in zip(P.codes, syndromes, llrs):
+        b, dev = s.shape[0], s.device
+        ios.append({"syndromes": s, "llr": l,
+                    "e_hat": torch.empty((b, B.n), dtype=torch.uint8, device=dev),
+                    "conv": torch.empty((b, B.R), dtype=torch.uint8, device=dev),
+                    "iters": torch.empty((b, B.R), dtype=torch.int16, device=dev),
+                    "success": torch.empty((b,), dtype=torch.uint8, device=dev),
+                    "selected": torch.empty((b,), dtype=torch.int16, device=dev)})
+    ws = torch.empty(mbbp_plan_workspace_size(P, [s.shape[0] for s in syndromes]), dtype=torch.uint8,
+                     device=syndromes[0].device)
+    return ios, ws
 
 
 class Logicals:
