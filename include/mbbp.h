@@ -252,6 +252,62 @@ mbbp_status mbbp_plan_autotune(mbbp_plan* P, const mbbp_code_io* io, int iters, 
 mbbp_status mbbp_plan_info(const mbbp_plan* P, int32_t* warps, int32_t* chunk, int32_t* kind,
                            int32_t* order);
 
+/* ------------------------------------------------------------------------
+ * Differentiable weighted min-sum (WMS) and learned weights.
+ * ---------------------------------------------------------------------- */
+
+/* WMS is normalized min-sum (Section II-B, Eq. (2)-(3)) with a weight w and a
+ * damping factor g per edge and per iteration of every representation; the
+ * paper defines no such variant, w == alpha and g == 0 reproduces Eq. (2):
+ *   m^(t)_e = g^(t)_e m^(t-1)_e + (1 - g^(t)_e) w^(t)_e S_e mn_e,
+ *   S_e = (-1)^{s_c} prod_{other e' of c} sign(q^(t-1)_e'),
+ *   mn_e = min(LMAX, min_{other e' of c} |q^(t-1)_e'|),
+ *   q^(t)_e = mu_v + sum_{other e' of v} m^(t)_e', m^(0) = 0, q^(0) = mu,
+ * for t = 1..T (flooding, no early stop); loss of a (shot, representation):
+ *   scale * sum_v BCE(sigmoid(-post_v), e_v), post = mu + sum_c m^(T).
+ * w and g are device float[R][T][E], E = the largest edge count of the
+ * representations (mbbp_bases_info), edges numbered row by row of H^(t),
+ * columns ascending. */
+
+/* Workspace of mbbp_wms_forward / mbbp_wms_backward: the checkpoints of m,
+ * one every `ckpt` iterations ((T-1)/ckpt of them per (shot, representation)). */
+size_t mbbp_wms_workspace_size(const mbbp_bases* B, int batch, int T, int ckpt);
+
+/* Forward pass.  syndromes, llr, llr_stride: as mbbp_decode.  etrue: device
+ * uint8[batch*n] true errors or NULL; posterior: device float[batch*R*n]
+ * (needed by the backward pass); loss: device float[batch*R] or NULL (needs
+ * etrue).  The workspace keeps the checkpoints for mbbp_wms_backward. */
+mbbp_status mbbp_wms_forward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
+                             int llr_stride, int T, const float* w, const float* g, int ckpt,
+                             const uint8_t* etrue, float scale, float* posterior, float* loss,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
+/* Backward pass (hand-written adjoint): adds dL/dw and dL/dg (device
+ * float[R][T][E]) of the summed loss of every (shot, representation).  The
+ * inputs, posterior and workspace must be those of the forward call.  The
+ * min's derivative goes to the other edge of the check with the smallest
+ * |q| (lowest index on ties) when it is below LMAX, times sign(q) (+1 at 0);
+ * the sign's derivative is 0.  Segments of `ckpt` iterations are recomputed
+ * from their checkpoint.  Accumulation order varies (atomics). */
+mbbp_status mbbp_wms_backward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
+                              int llr_stride, int T, const float* w, const float* g, int ckpt,
+                              const uint8_t* etrue, float scale, const float* posterior, float* gw,
+                              float* gg, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Algorithm 1 with WMS as the BP of every representation: the halting rule
+ * after every iteration (up to `iters`; iterations past T use the weights of
+ * iteration T), then FWS.  Outputs and workspace as mbbp_decode. */
+mbbp_status mbbp_wms_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
+                            int llr_stride, int iters, int T, const float* w, const float* g,
+                            uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,
+                            int16_t* selected, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One Adam step on `count` device floats (params, grad, first and second
+ * moments m and v), bias-corrected with the 1-based step number; the updated
+ * parameters are clamped to [lo, hi]. */
+mbbp_status mbbp_adam_step(float* params, const float* grad, float* m, float* v, size_t count, float lr,
+                           float beta1, float beta2, float eps, int step, float lo, float hi, void* stream);
+
 /* Size of the fixed device scratch behind mbbp_decode_noalloc (8 MiB). */
 #define MBBP_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 

@@ -19,6 +19,8 @@ Functions and the passages they follow:
 ``fws``                    Frequency-Weighted Scoring (Section III-B)
 ``mbbp_decode``            Algorithm 1 over a batch of syndromes
 ``judge``                  logical-error test by GF(2) rank
+``wms_forward``            weighted min-sum, FP64 (a reading of Section II-B)
+``wms_backward``           its hand-written adjoint
 =========================  ====================================================
 
 Every function takes and returns numpy arrays.  ``precision`` is ``"f64"``
@@ -102,6 +104,13 @@ def _load():
                 fn.argtypes = [u8p, C.c_int, C.c_int, C.c_int, i32p, i32p,
                                C.c_int, u8p, fp, C.c_int, C.c_int, real, C.c_int,
                                u8p, u8p, vp, u8p, vp, vp, vp]
+            for name in ("or_wms_forward", "or_wms_backward"):
+                fn = getattr(lib, name)
+                fn.restype = C.c_double
+            lib.or_wms_forward.argtypes = [u8p, C.c_int, C.c_int, u8p, f64p, C.c_int, f64p, f64p,
+                                           vp, C.c_double, vp]
+            lib.or_wms_backward.argtypes = [u8p, C.c_int, C.c_int, u8p, f64p, C.c_int, f64p, f64p,
+                                            u8p, C.c_double, f64p, f64p]
             lib.or_judge.restype = None
             lib.or_judge.argtypes = [u8p, C.c_int, u8p, C.c_int, C.c_int, C.c_int,
                                      u8p, u8p, u8p]
@@ -262,6 +271,34 @@ def mbbp_decode(H, sets, synd, llr, iters: int, alpha: float,
     if want_post:
         out["post"] = post
     return out
+
+
+def wms_forward(Ht, st, mu, w, g, etrue=None, scale: float = 1.0):
+    """Weighted min-sum on one representation, FP64 (see mbbp_oracle.c).
+    w, g: [T, E] (edges row by row, columns ascending).  Returns
+    (loss, posterior) with loss = scale * sum_v BCE(sigmoid(-post_v), e_v)."""
+    Ht, st = _u8(Ht), _u8(st)
+    M, n = Ht.shape
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    post = np.zeros(n)
+    et = None if etrue is None else _u8(etrue)
+    L = _load().or_wms_forward(Ht, M, n, st, mu, w.shape[0], w, g, _ptr(et), scale, _ptr(post))
+    return float(L), post
+
+
+def wms_backward(Ht, st, mu, w, g, etrue, scale: float = 1.0):
+    """Adjoint of wms_forward: (loss, dL/dw [T, E], dL/dg [T, E])."""
+    Ht, st, et = _u8(Ht), _u8(st), _u8(etrue)
+    M, n = Ht.shape
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    gw = np.zeros_like(w)
+    gg = np.zeros_like(g)
+    L = _load().or_wms_backward(Ht, M, n, st, mu, w.shape[0], w, g, et, scale, gw, gg)
+    return float(L), gw, gg
 
 
 def judge(Hc, Ho, e, ehat) -> np.ndarray:

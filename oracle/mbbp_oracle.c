@@ -370,3 +370,198 @@ void or_judge(const uint8_t* Hc, int mc, const uint8_t* Ho, int mo, int n,
     }
     free(A);
 }
+
+/* ------------------------------------------------- weighted min-sum (WMS) -- */
+
+/* Differentiable weighted min-sum on one representation (FP64), a reading of
+ * the paper's normalized min-sum (Section II-B, Eq. (2)-(3)) with a weight
+ * and a damping factor per edge and per iteration; w == alpha and g == 0
+ * gives normalized min-sum (flooding, no early stop):
+ *   m^(t)_e = g^(t)_e m^(t-1)_e + (1 - g^(t)_e) w^(t)_e S_e mn_e,
+ *   S_e = (-1)^{s_c} prod_{other e' of c} sign(q^(t-1)_e'),
+ *   mn_e = min(LMAX, min_{other e' of c} |q^(t-1)_e'|),
+ *   q^(t)_e = mu_v + sum_{other e' of v} m^(t)_e' (ascending row order),
+ * with m^(0) = 0, q^(0) = mu, for t = 1..T.  Edges are numbered row by row,
+ * columns ascending; w and g are [T][E].  Loss of the item:
+ *   L = scale * sum_v BCE(sigmoid(-post_v), e_v),  post = mu + sum_c m^(T).
+ * Outputs post[n] and returns L. */
+static int or_wms_graph(const uint8_t* Ht, int M, int n, int** row_start, int** edge_col,
+                        int** col_start, int** col_edges)
+{
+    int E = 0;
+    for (int r = 0; r < M; r++)
+        for (int v = 0; v < n; v++) E += Ht[(size_t)r * n + v] ? 1 : 0;
+    *row_start = (int*)calloc((size_t)M + 1, sizeof(int));
+    *edge_col = (int*)malloc(sizeof(int) * (size_t)(E + 1));
+    *col_start = (int*)calloc((size_t)n + 1, sizeof(int));
+    *col_edges = (int*)malloc(sizeof(int) * (size_t)(E + 1));
+    int* fill = (int*)calloc((size_t)n + 1, sizeof(int));
+    int e = 0;
+    for (int r = 0; r < M; r++) {
+        (*row_start)[r] = e;
+        for (int v = 0; v < n; v++)
+            if (Ht[(size_t)r * n + v]) { (*edge_col)[e++] = v; (*col_start)[v + 1]++; }
+    }
+    (*row_start)[M] = e;
+    for (int v = 0; v < n; v++) (*col_start)[v + 1] += (*col_start)[v];
+    for (int k = 0; k < E; k++) {
+        int v = (*edge_col)[k];
+        (*col_edges)[(*col_start)[v] + fill[v]++] = k;
+    }
+    free(fill);
+    return E;
+}
+
+/* one WMS iteration: m_new from (m_prev, q_prev); then q_new and post */
+static void or_wms_step(int M, int n, const int* row_start, const int* col_start,
+                        const int* col_edges, const int* edge_col, const uint8_t* st,
+                        const double* mu, const double* w, const double* g,
+                        const double* m_prev, const double* q_prev, double* m_new,
+                        double* q_new, double* post)
+{
+    for (int r = 0; r < M; r++) {
+        int a = row_start[r], b = row_start[r + 1];
+        for (int j = a; j < b; j++) {
+            double mn = OR_LMAX;
+            int neg = st[r] & 1;
+            for (int k = a; k < b; k++) {
+                if (k == j) continue;
+                double x = fabs(q_prev[k]);
+                if (x < mn) mn = x;
+                if (q_prev[k] < 0) neg ^= 1;
+            }
+            double sgn = neg ? -1.0 : 1.0;
+            m_new[j] = g[j] * m_prev[j] + (1.0 - g[j]) * w[j] * sgn * mn;
+        }
+    }
+    for (int v = 0; v < n; v++) {
+        int a = col_start[v], b = col_start[v + 1];
+        double acc = mu[v];
+        for (int i = a; i < b; i++) acc = acc + m_new[col_edges[i]];
+        if (post) post[v] = acc;
+        for (int i = a; i < b; i++) {
+            double q = mu[v];
+            for (int k = a; k < b; k++) {
+                if (k == i) continue;
+                q = q + m_new[col_edges[k]];
+            }
+            q_new[col_edges[i]] = q;
+        }
+    }
+    (void)edge_col;
+}
+
+static double or_bce_sigmoid_neg(double post, int e)
+{
+    /* BCE(p, e) with p = sigmoid(-post) = P(e = 1), written stably:
+     * -log p = log(1 + exp(post)), -log(1 - p) = log(1 + exp(-post)) */
+    double x = e ? post : -post;
+    return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x));
+}
+
+double or_wms_forward(const uint8_t* Ht, int M, int n, const uint8_t* st, const double* mu,
+                      int T, const double* w, const double* g, const uint8_t* etrue,
+                      double scale, double* post_out)
+{
+    int *row_start, *edge_col, *col_start, *col_edges;
+    int E = or_wms_graph(Ht, M, n, &row_start, &edge_col, &col_start, &col_edges);
+    double* m_prev = (double*)calloc((size_t)E + 1, sizeof(double));
+    double* m_new = (double*)calloc((size_t)E + 1, sizeof(double));
+    double* q = (double*)calloc((size_t)E + 1, sizeof(double));
+    double* q_new = (double*)calloc((size_t)E + 1, sizeof(double));
+    double* post = (double*)calloc((size_t)n + 1, sizeof(double));
+    for (int k = 0; k < E; k++) q[k] = mu[edge_col[k]];
+    for (int v = 0; v < n; v++) post[v] = mu[v];
+    for (int t = 0; t < T; t++) {
+        or_wms_step(M, n, row_start, col_start, col_edges, edge_col, st, mu,
+                    w + (size_t)t * E, g + (size_t)t * E, m_prev, q, m_new, q_new, post);
+        double* tmp = m_prev; m_prev = m_new; m_new = tmp;
+        tmp = q; q = q_new; q_new = tmp;
+    }
+    double L = 0;
+    for (int v = 0; v < n; v++) {
+        if (post_out) post_out[v] = post[v];
+        if (etrue) L += or_bce_sigmoid_neg(post[v], etrue[v] & 1);
+    }
+    free(row_start); free(edge_col); free(col_start); free(col_edges);
+    free(m_prev); free(m_new); free(q); free(q_new); free(post);
+    return scale * L;
+}
+
+/* Adjoint of or_wms_forward: adds dL/dw and dL/dg ([T][E]) to gw, gg.  The
+ * derivative of the min goes to the other edge of the row with the smallest
+ * |q| (the lowest-numbered one on ties), times sign(q) (+1 at 0), when that
+ * |q| is below LMAX; the derivative of the sign is 0.  Returns L. */
+double or_wms_backward(const uint8_t* Ht, int M, int n, const uint8_t* st, const double* mu,
+                       int T, const double* w, const double* g, const uint8_t* etrue,
+                       double scale, double* gw, double* gg)
+{
+    int *row_start, *edge_col, *col_start, *col_edges;
+    int E = or_wms_graph(Ht, M, n, &row_start, &edge_col, &col_start, &col_edges);
+    /* forward, keeping every m^(t) and q^(t) */
+    double* ms = (double*)calloc((size_t)(T + 1) * E + 1, sizeof(double));
+    double* qs = (double*)calloc((size_t)(T + 1) * E + 1, sizeof(double));
+    double* post = (double*)calloc((size_t)n + 1, sizeof(double));
+    for (int k = 0; k < E; k++) qs[k] = mu[edge_col[k]];
+    for (int v = 0; v < n; v++) post[v] = mu[v];
+    for (int t = 0; t < T; t++)
+        or_wms_step(M, n, row_start, col_start, col_edges, edge_col, st, mu,
+                    w + (size_t)t * E, g + (size_t)t * E, ms + (size_t)t * E,
+                    qs + (size_t)t * E, ms + (size_t)(t + 1) * E, qs + (size_t)(t + 1) * E, post);
+    double L = 0;
+    double* gm = (double*)calloc((size_t)E + 1, sizeof(double));   /* dL/dm^(t) */
+    double* gm_prev = (double*)calloc((size_t)E + 1, sizeof(double));
+    double* gq = (double*)calloc((size_t)E + 1, sizeof(double));   /* dL/dq^(t-1) */
+    for (int v = 0; v < n; v++) {
+        int e = etrue[v] & 1;
+        L += or_bce_sigmoid_neg(post[v], e);
+        /* dBCE/dpost = e - sigmoid(-post) */
+        double p = 1.0 / (1.0 + exp(post[v]));
+        double gp = scale * ((double)e - p);
+        for (int i = col_start[v]; i < col_start[v + 1]; i++) gm[col_edges[i]] = gp;
+    }
+    for (int t = T; t >= 1; t--) {
+        const double* m_prev = ms + (size_t)(t - 1) * E;
+        const double* q_prev = qs + (size_t)(t - 1) * E;
+        const double* wt = w + (size_t)(t - 1) * E;
+        const double* gt = g + (size_t)(t - 1) * E;
+        for (int k = 0; k < E; k++) gq[k] = 0;
+        for (int r = 0; r < M; r++) {
+            int a = row_start[r], b = row_start[r + 1];
+            for (int j = a; j < b; j++) {
+                double mn = OR_LMAX;
+                int neg = st[r] & 1, arg = -1;
+                for (int k = a; k < b; k++) {
+                    if (k == j) continue;
+                    double x = fabs(q_prev[k]);
+                    if (x < mn) { mn = x; arg = k; }
+                    if (q_prev[k] < 0) neg ^= 1;
+                }
+                double sgn = neg ? -1.0 : 1.0;
+                double c = wt[j] * sgn * mn;
+                gg[(size_t)(t - 1) * E + j] += gm[j] * (m_prev[j] - c);
+                gw[(size_t)(t - 1) * E + j] += gm[j] * (1.0 - gt[j]) * sgn * mn;
+                gm_prev[j] = gm[j] * gt[j];
+                if (arg >= 0) {
+                    double gmn = gm[j] * (1.0 - gt[j]) * wt[j] * sgn;
+                    gq[arg] += gmn * (q_prev[arg] < 0 ? -1.0 : 1.0);
+                }
+            }
+        }
+        /* q^(t-1)_e = mu + sum_{other e'} m^(t-1)_e'  (q^(0) = mu has no m) */
+        if (t >= 2) {
+            for (int v = 0; v < n; v++) {
+                double G = 0;
+                for (int i = col_start[v]; i < col_start[v + 1]; i++) G += gq[col_edges[i]];
+                for (int i = col_start[v]; i < col_start[v + 1]; i++) {
+                    int e = col_edges[i];
+                    gm_prev[e] += G - gq[e];
+                }
+            }
+        }
+        double* tmp = gm; gm = gm_prev; gm_prev = tmp;
+    }
+    free(row_start); free(edge_col); free(col_start); free(col_edges);
+    free(ms); free(qs); free(post); free(gm); free(gm_prev); free(gq);
+    return scale * L;
+}

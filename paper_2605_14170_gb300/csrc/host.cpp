@@ -348,6 +348,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     B->set_rows.assign(set_rows ? set_rows : set_ptr, set_rows ? set_rows + set_ptr[R] : set_ptr);
 
     std::vector<uint32_t> rowinfo((size_t)R * MP, 0);
+    std::vector<int32_t> rowptr((size_t)R * MP, 0);
     std::vector<uint2> vdesc((size_t)R * n);
     std::vector<uint16_t> vslot;
     std::vector<int32_t> rows(R), edges(R);
@@ -361,6 +362,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
             const int src = r < m ? r : set_rows[set_ptr[t] + (r - m)];
             const auto& cols = g.rcols[src];
             rowinfo[(size_t)t * MP + r] = (uint32_t)src | ((uint32_t)cols.size() << 16) | (1u << 31);
+            rowptr[(size_t)t * MP + r] = E;
             for (int j = 0; j < (int)cols.size(); ++j) vl[cols[j]].push_back((uint16_t)(j * MP + r));
             E += (int)cols.size();
         }
@@ -454,7 +456,8 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     const size_t o_rows = o_vslot + align256(std::max<size_t>(vslot.size(), 1) * 2);
     const size_t o_hcol = o_rows + align256(rows.size() * 4);
     const size_t o_hmask = o_hcol + align256(hcol.size() * 2);
-    const size_t o_vdesc2 = o_hmask + align256(hmask.size() * 4);
+    const size_t o_rowptr = o_hmask + align256(hmask.size() * 4);
+    const size_t o_vdesc2 = o_rowptr + align256(rowptr.size() * 4);
     const size_t o_rinfo2 = o_vdesc2 + align256(vdesc2.size() * sizeof(uint4));
     const size_t o_hmask2 = o_rinfo2 + align256(rinfo2.size() * 4);
     const size_t total = o_hmask2 + align256(hmask2.size() * 4);
@@ -473,6 +476,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         {o_rows, rows.data(), rows.size() * 4},
         {o_hcol, hcol.data(), hcol.size() * 2},
         {o_hmask, hmask.data(), hmask.size() * 4},
+        {o_rowptr, rowptr.data(), rowptr.size() * 4},
         {o_vdesc2, vdesc2.data(), vdesc2.size() * sizeof(uint4)},
         {o_rinfo2, rinfo2.data(), rinfo2.size() * 4},
         {o_hmask2, hmask2.data(), hmask2.size() * 4},
@@ -493,6 +497,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     d.rows = reinterpret_cast<const int32_t*>(base + o_rows);
     d.hcol = reinterpret_cast<const uint16_t*>(base + o_hcol);
     d.hmask = reinterpret_cast<const uint32_t*>(base + o_hmask);
+    d.rowptr = reinterpret_cast<const int32_t*>(base + o_rowptr);
     d.m = m; d.n = n; d.R = R; d.DC = K; d.DV = dv; d.MP = MP; d.mpad = mpad; d.W = W;
     d.regular = B->regular;
     d.shape = shape;
@@ -948,6 +953,158 @@ mbbp_status mbbp_plan_autotune(mbbp_plan* P, const mbbp_code_io* io, int iters, 
     if (st != MBBP_OK) return st;
     if (best_ms) *best_ms = best;
     return MBBP_OK;
+}
+
+// -------------------------------------------------- weighted min-sum (WMS)
+
+namespace {
+
+int max_edges(const mbbp_bases* B) {
+    return *std::max_element(B->edges.begin(), B->edges.end());
+}
+
+mbbp_status wms_check(const mbbp_bases* B, int batch, int T, int ckpt) {
+    if (!B) return fail(MBBP_E_INVALID, "NULL handle");
+    if (batch < 0) return fail(MBBP_E_INVALID, "batch must be >= 0");
+    if (T < 1 || T > MBBP_MAX_ITERS) return fail(MBBP_E_INVALID, "T out of range");
+    if (ckpt < 1) return fail(MBBP_E_INVALID, "ckpt must be >= 1");
+    return check_device(B->device);
+}
+
+}  // namespace
+
+size_t mbbp_wms_workspace_size(const mbbp_bases* B, int batch, int T, int ckpt) {
+    if (!B || batch < 0 || T < 1 || ckpt < 1) return 0;
+    const size_t nckpt = (size_t)((T - 1) / ckpt);
+    return 256 + align256((size_t)batch * B->R * nckpt * B->dev.DC * B->MP * 4);
+}
+
+mbbp_status mbbp_wms_forward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
+                             int llr_stride, int T, const float* w, const float* g, int ckpt,
+                             const uint8_t* etrue, float scale, float* posterior, float* loss,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+    if (mbbp_status st = wms_check(B, batch, T, ckpt)) return st;
+    if (batch == 0) return MBBP_OK;
+    if (!syndromes || !llr || !w || !g || !posterior || !workspace)
+        return fail(MBBP_E_INVALID, "mbbp_wms_forward: NULL buffer");
+    if (loss && !etrue) return fail(MBBP_E_INVALID, "loss needs etrue");
+    if (llr_stride != 0 && llr_stride < B->n) return fail(MBBP_E_INVALID, "llr_stride must be 0 or >= n");
+    if (workspace_bytes < mbbp_wms_workspace_size(B, batch, T, ckpt)) return fail(MBBP_E_INVALID, "workspace too small");
+    WmsArgs a{};
+    a.B = B->dev;
+    a.synd = syndromes;
+    a.llr = llr;
+    a.llr_stride = llr_stride;
+    a.T = T;
+    a.ckpt = ckpt;
+    a.nckpt = (T - 1) / ckpt;
+    a.E = max_edges(B);
+    a.w = w;
+    a.g = g;
+    a.etrue = etrue;
+    a.scale = scale;
+    a.post = posterior;
+    a.loss = loss;
+    a.counter = static_cast<unsigned long long*>(workspace);
+    a.ckpt_buf = a.nckpt ? reinterpret_cast<float*>(static_cast<char*>(workspace) + 256) : nullptr;
+    a.total_items = (unsigned long long)batch * B->R;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, 8, s);
+    if (e == cudaSuccess) e = launch_wms(a, false, s, B->sm_count);
+    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_wms_forward");
+}
+
+mbbp_status mbbp_wms_backward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
+                              int llr_stride, int T, const float* w, const float* g, int ckpt,
+                              const uint8_t* etrue, float scale, const float* posterior, float* gw,
+                              float* gg, void* workspace, size_t workspace_bytes, void* stream) {
+    if (mbbp_status st = wms_check(B, batch, T, ckpt)) return st;
+    if (batch == 0) return MBBP_OK;
+    if (!syndromes || !llr || !w || !g || !etrue || !posterior || !gw || !gg || !workspace)
+        return fail(MBBP_E_INVALID, "mbbp_wms_backward: NULL buffer");
+    if (llr_stride != 0 && llr_stride < B->n) return fail(MBBP_E_INVALID, "llr_stride must be 0 or >= n");
+    if (workspace_bytes < mbbp_wms_workspace_size(B, batch, T, ckpt)) return fail(MBBP_E_INVALID, "workspace too small");
+    WmsArgs a{};
+    a.B = B->dev;
+    a.synd = syndromes;
+    a.llr = llr;
+    a.llr_stride = llr_stride;
+    a.T = T;
+    a.ckpt = ckpt;
+    a.nckpt = (T - 1) / ckpt;
+    a.E = max_edges(B);
+    a.w = w;
+    a.g = g;
+    a.etrue = etrue;
+    a.scale = scale;
+    a.post = const_cast<float*>(posterior);
+    a.gw = gw;
+    a.gg = gg;
+    a.counter = static_cast<unsigned long long*>(workspace);
+    a.ckpt_buf = a.nckpt ? reinterpret_cast<float*>(static_cast<char*>(workspace) + 256) : nullptr;
+    a.total_items = (unsigned long long)batch * B->R;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, 8, s);
+    if (e == cudaSuccess) e = launch_wms(a, true, s, B->sm_count);
+    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_wms_backward");
+}
+
+mbbp_status mbbp_wms_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
+                            int llr_stride, int iters, int T, const float* w, const float* g,
+                            uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,
+                            int16_t* selected, void* workspace, size_t workspace_bytes, void* stream) {
+    if (mbbp_status st = wms_check(B, batch, T, 1)) return st;
+    if (iters < 0 || iters > MBBP_MAX_ITERS) return fail(MBBP_E_INVALID, "iters out of range");
+    if (batch == 0) return MBBP_OK;
+    if (!syndromes || !llr || !w || !g || !e_hat || !conv || !success || !workspace)
+        return fail(MBBP_E_INVALID, "mbbp_wms_decode: NULL buffer");
+    if (llr_stride != 0 && llr_stride < B->n) return fail(MBBP_E_INVALID, "llr_stride must be 0 or >= n");
+    if (workspace_bytes < mbbp_decode_workspace_size(B, batch)) return fail(MBBP_E_INVALID, "workspace too small");
+    WmsArgs a{};
+    a.B = B->dev;
+    a.synd = syndromes;
+    a.llr = llr;
+    a.llr_stride = llr_stride;
+    a.T = T;
+    a.ckpt = 1;
+    a.E = max_edges(B);
+    a.w = w;
+    a.g = g;
+    a.decode = 1;
+    a.iters = iters;
+    const size_t cand_bytes = align256((size_t)batch * B->R * B->W * 4);
+    a.cand = static_cast<uint32_t*>(workspace);
+    a.counter = reinterpret_cast<unsigned long long*>(static_cast<char*>(workspace) + cand_bytes);
+    a.conv = conv;
+    a.iters_run = iters_run;
+    a.total_items = (unsigned long long)batch * B->R;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, 8, s);
+    if (e == cudaSuccess) e = launch_wms(a, false, s, B->sm_count);
+    if (e != cudaSuccess) return cuda_fail(e, "mbbp_wms_decode");
+    FwsArgs f{};
+    f.cand = a.cand;
+    f.conv = conv;
+    f.batch = batch;
+    f.R = B->R;
+    f.n = B->n;
+    f.W = B->W;
+    f.e_hat = e_hat;
+    f.success = success;
+    f.selected = selected;
+    e = launch_fws(f, s);
+    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_wms_decode (FWS)");
+}
+
+mbbp_status mbbp_adam_step(float* params, const float* grad, float* m, float* v, size_t count, float lr,
+                           float beta1, float beta2, float eps, int step, float lo, float hi, void* stream) {
+    if (count == 0) return MBBP_OK;
+    if (!params || !grad || !m || !v) return fail(MBBP_E_INVALID, "mbbp_adam_step: NULL buffer");
+    if (step < 1 || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f))
+        return fail(MBBP_E_INVALID, "mbbp_adam_step: bad hyper-parameters");
+    cudaError_t e = launch_adam(params, grad, m, v, count, lr, beta1, beta2, eps, step, lo, hi,
+                                (cudaStream_t)stream);
+    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_adam_step");
 }
 
 mbbp_status mbbp_logicals_build(const uint8_t* H, int m, const uint8_t* H_other, int m_other,

@@ -27,6 +27,7 @@ struct DevBases {
                               //         variables sorted by degree (stable)
     const uint16_t* vslot;    // slot ids of every variable, ascending row of H^(t)
     const int32_t* rows;      // [R] rows of H^(t)
+    const int32_t* rowptr;    // [R][MP] first edge of each row (edges numbered row by row)
     const uint16_t* hcol;     // [DC][mpad] columns of the rows of H (n = padding)
     const uint32_t* hmask;    // [m][W] rows of H as bit masks
     int m, n, R, DC, DV, MP, mpad, W;
@@ -108,6 +109,33 @@ struct MixedArgs {
 };
 size_t mixed_warp_bytes(const DevBases& B, int kind);
 cudaError_t launch_mixed(const MixedArgs& a, int warps, int rule, cudaStream_t s, int sm_count);
+
+// Weighted min-sum forward / backward / decode (wms.cu).
+struct WmsArgs {
+    DevBases B;
+    const uint8_t* synd;
+    const float* llr;
+    int llr_stride;
+    int T, ckpt, nckpt, E;      // iterations, checkpoint interval, stored checkpoints, edges per row of w/g
+    const float* w;             // [R][T][E]
+    const float* g;             // [R][T][E]
+    const uint8_t* etrue;       // [batch][n] or null
+    float scale;
+    float* post;                // [batch][R][n]
+    float* loss;                // [batch][R] or null
+    float* ckpt_buf;            // [batch][R][nckpt][DC*MP]
+    float* gw;                  // [R][T][E]
+    float* gg;
+    int decode, iters;          // decode mode: halting rule, candidates
+    uint32_t* cand;
+    uint8_t* conv;
+    uint16_t* iters_run;
+    unsigned long long* counter;
+    unsigned long long total_items;
+};
+cudaError_t launch_wms(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count);
+cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, size_t count, float lr, float b1,
+                        float b2, float eps, int step, float lo, float hi, cudaStream_t s);
 
 // Launchers (decode.cu, decode_small.cu, aux.cu).  They return cudaGetLastError().
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count);

@@ -1,0 +1,441 @@
+// Differentiable weighted min-sum (WMS): the normalized min-sum of Section
+// II-B (Eq. (2)-(3)) with a weight w and a damping factor g per edge and per
+// iteration of every representation H^(t), unrolled for T flooding
+// iterations; w == alpha, g == 0 is normalized min-sum:
+//   m^(t)_e = g^(t)_e m^(t-1)_e + (1 - g^(t)_e) w^(t)_e S_e mn_e,
+//   S_e = (-1)^{s_c} prod_{other e' of c} sign(q^(t-1)_e'),
+//   mn_e = min(LMAX, min_{other e' of c} |q^(t-1)_e'|),
+//   q^(t)_e = mu_v + sum_{other e' of v} m^(t)_e',  m^(0) = 0, q^(0) = mu.
+// Loss of an item: scale * sum_v BCE(sigmoid(-post_v), e_v), post = mu + sum m^(T).
+//
+// Kernels (one warp per (shot, representation), generic slot layout):
+//   wms_forward   T iterations, posterior, loss, a checkpoint of m every
+//                 `ckpt` iterations; or, in decode mode, the halting rule
+//                 after every iteration and the candidate for FWS
+//                 (iterations past T reuse the weights of iteration T);
+//   wms_backward  segment by segment from the last checkpoint: recompute the
+//                 segment's forward states, then the adjoint through it
+//                 (the min's derivative goes to the arg-min edge, lowest index
+//                 on ties; the sign's derivative is 0); parameter gradients are
+//                 added to gw / gg with atomics;
+//   adam_step     Adam update of the parameters, clamped to [lo, hi].
+#include "bp_generic.cuh"
+
+namespace mbbp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWmsWarps = 4;
+
+struct WmsLayout {
+    int S, npad, ehpad;
+    size_t fwd_bytes, bwd_bytes;
+};
+
+__host__ __device__ inline WmsLayout wms_layout(int DC, int MP, int n, int ckpt) {
+    WmsLayout L;
+    L.S = DC * MP;
+    L.npad = (n + 4) & ~3;
+    L.ehpad = (n + 1 + 15) & ~15;
+    // forward: m, q (S each), mu, post (npad each), hard decision bytes
+    L.fwd_bytes = (size_t)(2 * L.S + 2 * L.npad) * 4 + L.ehpad;
+    // backward: ckpt + 1 states of m, q, gm, gm_prev, gq (S each), mu (npad, with room for one more)
+    L.bwd_bytes = (size_t)((ckpt + 1) * L.S + 4 * L.S + 2 * L.npad) * 4;
+    return L;
+}
+
+// q^(t)_e and the posterior from m (variable pass, ascending row order).
+template <int DV>
+__device__ __forceinline__ void wms_var_pass(const DevBases& B, const uint2* vd, const float* m,
+                                             float* q, const float* mu, float* post) {
+    const int lane = threadIdx.x & 31;
+    for (int p = lane; p < B.n; p += 32) {
+        const uint2 d = __ldg(vd + p);
+        const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
+        const uint16_t* sl = B.vslot + d.x;
+        float acc = mu[v];
+        for (int i = 0; i < deg; ++i) acc = __fadd_rn(acc, m[__ldg(sl + i)]);
+        if (post) post[v] = acc;
+        for (int i = 0; i < deg; ++i) {
+            float x = mu[v];
+            for (int k = 0; k < deg; ++k)
+                if (k != i) x = __fadd_rn(x, m[__ldg(sl + k)]);
+            q[__ldg(sl + i)] = x;
+        }
+    }
+}
+
+// One WMS check pass: m <- g m + (1 - g) w S mn(q).  wt, gt: parameters of
+// this iteration for representation b ([E] in row-major edge order).
+template <int DC>
+__device__ __forceinline__ void wms_check_pass(const DevBases& B, int b, const uint32_t* rinfo,
+                                               int Mb, uint32_t sb, const float* q, float* m,
+                                               const float* wt, const float* gt) {
+    const int lane = threadIdx.x & 31;
+    const int MP = B.MP;
+    const int32_t* rp = B.rowptr + (size_t)b * MP;
+    for (int k = 0; k < (MP >> 5); ++k) {
+        const int r = lane + 32 * k;
+        if (r >= Mb) continue;
+        const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
+        const int e0 = __ldg(rp + r);
+        float qq[DC];
+#pragma unroll
+        for (int j = 0; j < DC; ++j) qq[j] = (j < deg) ? q[j * MP + r] : MBBP_LMAX;
+        const uint32_t s = (sb >> k) & 1u;
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            if (j >= deg) continue;
+            float mn = MBBP_LMAX;
+            uint32_t neg = s;
+#pragma unroll
+            for (int t = 0; t < DC; ++t) {
+                if (t == j || t >= deg) continue;
+                mn = fminf(mn, fabsf(qq[t]));
+                neg ^= (qq[t] < 0.f) ? 1u : 0u;
+            }
+            const float c = __fmul_rn(__ldg(wt + e0 + j), neg ? -mn : mn);
+            const float gg = __ldg(gt + e0 + j);
+            const float mo = m[j * MP + r];
+            m[j * MP + r] = __fadd_rn(__fmul_rn(gg, mo), __fmul_rn(__fsub_rn(1.0f, gg), c));
+        }
+    }
+}
+
+__device__ __forceinline__ float bce_neg_sigmoid(float post, int e) {
+    const float x = e ? post : -post;
+    return x > 0.f ? x + log1pf(expf(-x)) : log1pf(expf(x));
+}
+
+template <int DC, int DV>
+__global__ void __launch_bounds__(kWmsWarps * 32)
+wms_forward_kernel(const WmsArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevBases& B = a.B;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int MP = B.MP, n = B.n, m_rows = B.m, R = B.R, W = B.W;
+    const WmsLayout L = wms_layout(DC, MP, n, a.ckpt);
+    float* m = reinterpret_cast<float*>(smem + warp * L.fwd_bytes);
+    float* q = m + L.S;
+    float* mu = q + L.S;
+    float* post = mu + L.npad;
+    uint8_t* eh = reinterpret_cast<uint8_t*>(post + L.npad);
+    const int orow_steps = B.mpad >> 5;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= a.total_items) break;
+        const int shot = (int)(item / (unsigned long long)R);
+        const int b = (int)(item - (unsigned long long)shot * R);
+        const uint32_t* rinfo = B.rowinfo + (size_t)b * MP;
+        const uint2* vd = B.vdesc + (size_t)b * n;
+        const int Mb = __ldg(B.rows + b);
+        const float* llr = a.llr + (size_t)shot * a.llr_stride;
+        const uint8_t* sy = a.synd + (size_t)shot * m_rows;
+        for (int v = lane; v < n; v += 32) {
+            const float x = __ldg(llr + v);
+            mu[v] = x;
+            post[v] = x;
+            eh[v] = (x < 0.f) ? 1 : 0;
+        }
+        if (lane == 0) eh[n] = 0;
+        for (int i = lane; i < L.S; i += 32) m[i] = 0.0f;
+        uint32_t sb = 0;
+        for (int k = 0; k < (MP >> 5); ++k) {
+            const int r = lane + 32 * k;
+            if (r < Mb) sb |= (uint32_t)(__ldg(sy + (__ldg(rinfo + r) & 0xffffu)) & 1u) << k;
+        }
+        __syncwarp();
+        for (int p = lane; p < n; p += 32) {  // q^(0) = mu
+            const uint2 d = __ldg(vd + p);
+            const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
+            for (int i = 0; i < deg; ++i) q[__ldg(B.vslot + d.x + i)] = mu[v];
+        }
+        __syncwarp();
+        int K = 0;
+        bool conv = false;
+        const int iters = a.decode ? a.iters : a.T;
+        for (int it = 0;; ++it) {
+            if (a.decode) {
+                bool ok = true;
+                for (int k = 0; k < orow_steps; ++k) {
+                    const int r = lane + 32 * k;
+                    if (r < m_rows) {
+                        uint32_t par = (sb >> k) & 1u;
+#pragma unroll
+                        for (int j = 0; j < DC; ++j) par ^= eh[__ldg(B.hcol + j * B.mpad + r)];
+                        ok = ok && (par == 0u);
+                    }
+                }
+                if (__all_sync(kFull, ok)) {
+                    conv = true;
+                    K = it;
+                    break;
+                }
+            }
+            if (it == iters) {
+                K = it;
+                break;
+            }
+            const int tp = min(it, a.T - 1);  // iterations past T reuse the last weights
+            const float* wt = a.w + ((size_t)b * a.T + tp) * a.E;
+            const float* gt = a.g + ((size_t)b * a.T + tp) * a.E;
+            wms_check_pass<DC>(B, b, rinfo, Mb, sb, q, m, wt, gt);
+            __syncwarp();
+            wms_var_pass<DV>(B, vd, m, q, mu, post);
+            __syncwarp();
+            if (a.decode) {
+                for (int v = lane; v < n; v += 32) eh[v] = (post[v] < 0.f) ? 1 : 0;
+                __syncwarp();
+            } else if (a.ckpt_buf && (it + 1) % a.ckpt == 0 && it + 1 < a.T) {
+                float* dst = a.ckpt_buf + ((size_t)item * a.nckpt + ((it + 1) / a.ckpt - 1)) * L.S;
+                for (int i = lane; i < L.S; i += 32) dst[i] = m[i];
+            }
+        }
+        if (a.post)
+            for (int v = lane; v < n; v += 32) a.post[item * n + v] = post[v];
+        if (a.decode) {
+            uint32_t myword = 0;
+            for (int w = 0; w < W; ++w) {
+                const int v = 32 * w + lane;
+                const uint32_t word = __ballot_sync(kFull, v < n && eh[v]);
+                if ((w & 31) == lane) myword = word;
+                if ((w & 31) == 31 || w == W - 1) {
+                    const int base = w & ~31;
+                    if (base + lane <= w) a.cand[item * W + base + lane] = myword;
+                }
+            }
+            if (lane == 0) {
+                a.conv[item] = conv ? 1 : 0;
+                if (a.iters_run) a.iters_run[item] = (uint16_t)K;
+            }
+        } else if (a.etrue && a.loss) {
+            float acc = 0.f;
+            for (int v = lane; v < n; v += 32)
+                acc += bce_neg_sigmoid(post[v], a.etrue[(size_t)shot * n + v] & 1);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+            if (lane == 0) a.loss[item] = a.scale * acc;
+        }
+        __syncwarp();
+    }
+}
+
+template <int DC, int DV>
+__global__ void __launch_bounds__(kWmsWarps * 32)
+wms_backward_kernel(const WmsArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevBases& B = a.B;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int MP = B.MP, n = B.n, m_rows = B.m, R = B.R;
+    const WmsLayout L = wms_layout(DC, MP, n, a.ckpt);
+    float* states = reinterpret_cast<float*>(smem + warp * L.bwd_bytes);  // [ckpt + 1][S]
+    float* q = states + (size_t)(a.ckpt + 1) * L.S;
+    float* gm = q + L.S;
+    float* gmp = gm + L.S;
+    float* gq = gmp + L.S;
+    float* mu = gq + L.S;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= a.total_items) break;
+        const int shot = (int)(item / (unsigned long long)R);
+        const int b = (int)(item - (unsigned long long)shot * R);
+        const uint32_t* rinfo = B.rowinfo + (size_t)b * MP;
+        const uint2* vd = B.vdesc + (size_t)b * n;
+        const int32_t* rp = B.rowptr + (size_t)b * MP;
+        const int Mb = __ldg(B.rows + b);
+        const float* llr = a.llr + (size_t)shot * a.llr_stride;
+        const uint8_t* sy = a.synd + (size_t)shot * m_rows;
+        for (int v = lane; v < n; v += 32) mu[v] = __ldg(llr + v);
+        uint32_t sb = 0;
+        for (int k = 0; k < (MP >> 5); ++k) {
+            const int r = lane + 32 * k;
+            if (r < Mb) sb |= (uint32_t)(__ldg(sy + (__ldg(rinfo + r) & 0xffffu)) & 1u) << k;
+        }
+        for (int i = lane; i < L.S; i += 32) gm[i] = 0.0f;
+        __syncwarp();
+        // dL/dm^(T)_e = scale (e_v - sigmoid(-post_v)) on every edge of v
+        for (int p = lane; p < n; p += 32) {
+            const uint2 d = __ldg(vd + p);
+            const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
+            const float pv = __ldg(a.post + item * n + v);
+            const float sig = 1.0f / (1.0f + expf(pv));
+            const float gp = a.scale * ((float)(a.etrue[(size_t)shot * n + v] & 1) - sig);
+            for (int i = 0; i < deg; ++i) gm[__ldg(B.vslot + d.x + i)] = gp;
+        }
+        __syncwarp();
+        const int nseg = (a.T + a.ckpt - 1) / a.ckpt;
+        for (int seg = nseg - 1; seg >= 0; --seg) {
+            const int t0 = seg * a.ckpt;
+            const int t1 = min(a.T, t0 + a.ckpt);
+            // states[0] = m^(t0): zero or a checkpoint
+            if (t0 == 0) {
+                for (int i = lane; i < L.S; i += 32) states[i] = 0.0f;
+            } else {
+                const float* src = a.ckpt_buf + ((size_t)item * a.nckpt + (t0 / a.ckpt - 1)) * L.S;
+                for (int i = lane; i < L.S; i += 32) states[i] = src[i];
+            }
+            __syncwarp();
+            // recompute m^(t0+1 .. t1 - 1) (the adjoint needs m^(t-1) and q^(t-1))
+            for (int t = t0 + 1; t < t1; ++t) {
+                float* mprev = states + (size_t)(t - 1 - t0) * L.S;
+                float* mcur = states + (size_t)(t - t0) * L.S;
+                if (t - 1 == 0) {
+                    for (int p = lane; p < n; p += 32) {
+                        const uint2 d = __ldg(vd + p);
+                        const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
+                        for (int i = 0; i < deg; ++i) q[__ldg(B.vslot + d.x + i)] = mu[v];
+                    }
+                } else {
+                    wms_var_pass<DV>(B, vd, mprev, q, mu, nullptr);
+                }
+                for (int i = lane; i < L.S; i += 32) mcur[i] = mprev[i];
+                __syncwarp();
+                const float* wt = a.w + ((size_t)b * a.T + (t - 1)) * a.E;
+                const float* gt = a.g + ((size_t)b * a.T + (t - 1)) * a.E;
+                wms_check_pass<DC>(B, b, rinfo, Mb, sb, q, mcur, wt, gt);
+                __syncwarp();
+            }
+            // adjoint of iterations t1 .. t0 + 1
+            for (int t = t1; t > t0; --t) {
+                const float* mprev = states + (size_t)(t - 1 - t0) * L.S;
+                if (t - 1 == 0) {
+                    for (int p = lane; p < n; p += 32) {
+                        const uint2 d = __ldg(vd + p);
+                        const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
+                        for (int i = 0; i < deg; ++i) q[__ldg(B.vslot + d.x + i)] = mu[v];
+                    }
+                } else {
+                    wms_var_pass<DV>(B, vd, mprev, q, mu, nullptr);
+                }
+                for (int i = lane; i < L.S; i += 32) gq[i] = 0.0f;
+                __syncwarp();
+                const float* wt = a.w + ((size_t)b * a.T + (t - 1)) * a.E;
+                const float* gt = a.g + ((size_t)b * a.T + (t - 1)) * a.E;
+                float* gwt = a.gw + ((size_t)b * a.T + (t - 1)) * a.E;
+                float* ggt = a.gg + ((size_t)b * a.T + (t - 1)) * a.E;
+                for (int k = 0; k < (MP >> 5); ++k) {
+                    const int r = lane + 32 * k;
+                    if (r >= Mb) continue;
+                    const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
+                    const int e0 = __ldg(rp + r);
+                    float qq[DC], gacc[DC];
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        qq[j] = (j < deg) ? q[j * MP + r] : MBBP_LMAX;
+                        gacc[j] = 0.0f;
+                    }
+                    const uint32_t s = (sb >> k) & 1u;
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        if (j >= deg) continue;
+                        float mn = MBBP_LMAX;
+                        int arg = -1;
+                        uint32_t neg = s;
+#pragma unroll
+                        for (int u = 0; u < DC; ++u) {
+                            if (u == j || u >= deg) continue;
+                            const float x = fabsf(qq[u]);
+                            if (x < mn) { mn = x; arg = u; }
+                            neg ^= (qq[u] < 0.f) ? 1u : 0u;
+                        }
+                        const float sgn = neg ? -1.0f : 1.0f;
+                        const float ww = __ldg(wt + e0 + j), gg = __ldg(gt + e0 + j);
+                        const float gmj = gm[j * MP + r];
+                        const float c = ww * sgn * mn;
+                        atomicAdd(ggt + e0 + j, gmj * (mprev[j * MP + r] - c));
+                        atomicAdd(gwt + e0 + j, gmj * (1.0f - gg) * sgn * mn);
+                        gmp[j * MP + r] = gmj * gg;
+                        const float gmn = gmj * (1.0f - gg) * ww * sgn;
+#pragma unroll
+                        for (int u = 0; u < DC; ++u)
+                            if (u == arg) gacc[u] += gmn * (qq[u] < 0.f ? -1.0f : 1.0f);
+                    }
+#pragma unroll
+                    for (int j = 0; j < DC; ++j)
+                        if (j < deg) gq[j * MP + r] = gacc[j];
+                }
+                __syncwarp();
+                if (t >= 2) {
+                    for (int p = lane; p < n; p += 32) {
+                        const uint2 d = __ldg(vd + p);
+                        const int deg = (int)(d.y >> 16);
+                        const uint16_t* sl = B.vslot + d.x;
+                        float G = 0.0f;
+                        for (int i = 0; i < deg; ++i) G += gq[__ldg(sl + i)];
+                        for (int i = 0; i < deg; ++i) {
+                            const int e = __ldg(sl + i);
+                            gmp[e] += G - gq[e];
+                        }
+                    }
+                }
+                __syncwarp();
+                for (int i = lane; i < L.S; i += 32) gm[i] = gmp[i];
+                __syncwarp();
+            }
+        }
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ grad, float* __restrict__ m1,
+                            float* __restrict__ m2, size_t count, float lr, float b1, float b2, float eps,
+                            float c1, float c2, float lo, float hi) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = grad[i];
+    const float a = b1 * m1[i] + (1.0f - b1) * gi;
+    const float v = b2 * m2[i] + (1.0f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float x = p[i] - lr * (a / c1) / (sqrtf(v / c2) + eps);
+    p[i] = fminf(fmaxf(x, lo), hi);
+}
+
+template <int K>
+cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count) {
+    const WmsLayout L = wms_layout(K, a.B.MP, a.B.n, a.ckpt);
+    const size_t per_warp = backward ? L.bwd_bytes : L.fwd_bytes;
+    int warps = kWmsWarps;
+    while (warps > 1 && warps * per_warp > 200 * 1024) --warps;
+    if (per_warp > 200 * 1024) return cudaErrorInvalidConfiguration;
+    const size_t smem = warps * per_warp;
+    const void* kern = backward ? reinterpret_cast<const void*>(wms_backward_kernel<K, K>)
+                                : reinterpret_cast<const void*>(wms_forward_kernel<K, K>);
+    int per_sm = 0;
+    cudaError_t e = prepare_kernel(kern, warps * 32, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    unsigned long long want = (a.total_items + warps - 1) / warps;
+    unsigned long long grid = (unsigned long long)per_sm * sm_count;
+    if (want < grid) grid = want;
+    if (backward)
+        wms_backward_kernel<K, K><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    else
+        wms_forward_kernel<K, K><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_wms(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count) {
+    if (a.B.DC == 6) return launch_wms_t<6>(a, backward, s, sm_count);
+    if (a.B.DC == 8) return launch_wms_t<8>(a, backward, s, sm_count);
+    if (a.B.DC == 12) return launch_wms_t<12>(a, backward, s, sm_count);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, size_t count, float lr, float b1,
+                        float b2, float eps, int step, float lo, float hi, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    const float c1 = 1.0f - powf(b1, (float)step);
+    const float c2 = 1.0f - powf(b2, (float)step);
+    const unsigned grid = (unsigned)((count + 255) / 256);
+    adam_kernel<<<grid, 256, 0, s>>>(p, g, m1, m2, count, lr, b1, b2, eps, c1, c2, lo, hi);
+    return cudaGetLastError();
+}
+
+}  // namespace mbbp

@@ -79,6 +79,15 @@ _sig = {
     "mbbp_plan_autotune": (C.c_int, [_vp, C.POINTER(CodeIO), C.c_int, C.c_float, C.c_int, _vp,
                                      C.c_size_t, _vp, C.POINTER(C.c_float)]),
     "mbbp_plan_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "mbbp_wms_workspace_size": (C.c_size_t, [_vp, C.c_int, C.c_int, C.c_int]),
+    "mbbp_wms_forward": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp,
+                                   C.c_float, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "mbbp_wms_backward": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp,
+                                    C.c_float, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "mbbp_wms_decode": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "mbbp_adam_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_size_t, C.c_float, C.c_float, C.c_float,
+                                 C.c_float, C.c_int, C.c_float, C.c_float, _vp]),
     "mbbp_logicals_build": (C.c_int, [_u8p, C.c_int, _u8p, C.c_int, C.c_int, C.POINTER(_vp)]),
     "mbbp_logicals_info": (C.c_int, [_vp, _vp, _vp]),
     "mbbp_judge": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
@@ -363,6 +372,128 @@ def mixed_buffers(P: Plan, syndromes, llrs) -> tuple[list, object]:
     ws = torch.empty(mbbp_plan_workspace_size(P, [s.shape[0] for s in syndromes]), dtype=torch.uint8,
                      device=syndromes[0].device)
     return ios, ws
+
+
+# ----------------------------------------------------------- weighted min-sum
+
+def wms_params(B: Bases, T: int, alpha: float = 0.625, device="cuda"):
+    """(w, g) initialised to normalized min-sum: w = alpha, g = 0, shape
+    [R, T, E] with E the largest edge count of the representations."""
+    import torch
+    E = int(B.edges.max())
+    w = torch.full((B.R, T, E), float(alpha), dtype=torch.float32, device=device)
+    g = torch.zeros((B.R, T, E), dtype=torch.float32, device=device)
+    return w, g
+
+
+def mbbp_wms_workspace_size(B: Bases, batch: int, T: int, ckpt: int) -> int:
+    return int(_lib.mbbp_wms_workspace_size(B.handle, batch, T, ckpt))
+
+
+def _llr_stride(llr):
+    return 0 if llr.dim() == 1 else llr.shape[-1]
+
+
+def mbbp_wms_forward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, posterior, loss, workspace,
+                     stream=None) -> None:
+    import torch
+    _check(_lib.mbbp_wms_forward(
+        B.handle, syndromes.shape[0], _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
+        _llr_stride(llr), T, _dptr(w, torch.float32, "w"), _dptr(g, torch.float32, "g"), ckpt,
+        _dptr(etrue, torch.uint8, "etrue"), float(scale), _dptr(posterior, torch.float32, "posterior"),
+        _dptr(loss, torch.float32, "loss"), _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
+        _stream(stream)), "mbbp_wms_forward")
+
+
+def mbbp_wms_backward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, posterior, gw, gg, workspace,
+                      stream=None) -> None:
+    import torch
+    _check(_lib.mbbp_wms_backward(
+        B.handle, syndromes.shape[0], _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
+        _llr_stride(llr), T, _dptr(w, torch.float32, "w"), _dptr(g, torch.float32, "g"), ckpt,
+        _dptr(etrue, torch.uint8, "etrue"), float(scale), _dptr(posterior, torch.float32, "posterior"),
+        _dptr(gw, torch.float32, "gw"), _dptr(gg, torch.float32, "gg"), _dptr(workspace, torch.uint8, "workspace"),
+        workspace.numel(), _stream(stream)), "mbbp_wms_backward")
+
+
+def mbbp_wms_decode(B, syndromes, llr, iters, T, w, g, e_hat, conv, success, workspace, iters_run=None,
+                    selected=None, stream=None) -> None:
+    import torch
+    _check(_lib.mbbp_wms_decode(
+        B.handle, syndromes.shape[0], _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
+        _llr_stride(llr), iters, T, _dptr(w, torch.float32, "w"), _dptr(g, torch.float32, "g"),
+        _dptr(e_hat, torch.uint8, "e_hat"), _dptr(conv, torch.uint8, "conv"),
+        _dptr(iters_run, torch.int16, "iters_run"), _dptr(success, torch.uint8, "success"),
+        _dptr(selected, torch.int16, "selected"), _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
+        _stream(stream)), "mbbp_wms_decode")
+
+
+def mbbp_adam_step(params, grad, m, v, lr, beta1, beta2, eps, step, lo, hi, stream=None) -> None:
+    import torch
+    _check(_lib.mbbp_adam_step(_dptr(params, torch.float32, "params"), _dptr(grad, torch.float32, "grad"),
+                               _dptr(m, torch.float32, "m"), _dptr(v, torch.float32, "v"), params.numel(),
+                               float(lr), float(beta1), float(beta2), float(eps), int(step), float(lo), float(hi),
+                               _stream(stream)), "mbbp_adam_step")
+
+
+def wms_decode(B, syndromes, llr, iters, w, g) -> dict:
+    """Allocate outputs and run mbbp_wms_decode (T = w.shape[1])."""
+    import torch
+    dev = syndromes.device
+    batch = syndromes.shape[0]
+    out = {"e_hat": torch.empty((batch, B.n), dtype=torch.uint8, device=dev),
+           "conv": torch.empty((batch, B.R), dtype=torch.uint8, device=dev),
+           "iters": torch.empty((batch, B.R), dtype=torch.int16, device=dev),
+           "success": torch.empty((batch,), dtype=torch.uint8, device=dev),
+           "selected": torch.empty((batch,), dtype=torch.int16, device=dev)}
+    ws = torch.empty(mbbp_decode_workspace_size(B, batch), dtype=torch.uint8, device=dev)
+    mbbp_wms_decode(B, syndromes, llr, iters, w.shape[1], w, g, out["e_hat"], out["conv"], out["success"], ws,
+                    iters_run=out["iters"], selected=out["selected"])
+    return out
+
+
+def _wms_function():
+    import torch
+
+    class WMSLoss(torch.autograd.Function):
+        """Summed WMS loss of a batch; backward is the hand-written adjoint
+        kernel (mbbp_wms_backward) with checkpoints every `ckpt` iterations."""
+
+        @staticmethod
+        def forward(ctx, w, g, B, syndromes, llr, etrue, ckpt, scale):
+            T = w.shape[1]
+            batch = syndromes.shape[0]
+            post = torch.empty((batch, B.R, B.n), dtype=torch.float32, device=w.device)
+            loss = torch.empty((batch, B.R), dtype=torch.float32, device=w.device)
+            ws = torch.empty(mbbp_wms_workspace_size(B, batch, T, ckpt), dtype=torch.uint8, device=w.device)
+            mbbp_wms_forward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, post, loss, ws)
+            ctx.B, ctx.ckpt, ctx.scale = B, ckpt, scale
+            ctx.save_for_backward(w, g, syndromes, llr, etrue, post, ws)
+            return loss.sum()
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            w, g, syndromes, llr, etrue, post, ws = ctx.saved_tensors
+            gw = torch.zeros_like(w)
+            gg = torch.zeros_like(g)
+            mbbp_wms_backward(ctx.B, syndromes, llr, w.shape[1], w, g, ctx.ckpt, etrue, ctx.scale, post, gw, gg, ws)
+            return gw * grad_out, gg * grad_out, None, None, None, None, None, None
+
+    return WMSLoss
+
+
+_WMS_FN = None
+
+
+def wms_loss(w, g, B, syndromes, llr, etrue, ckpt: int = 5, scale: float | None = None):
+    """Differentiable WMS loss (mean BCE over shots, representations and
+    variables unless ``scale`` is given)."""
+    global _WMS_FN
+    if _WMS_FN is None:
+        _WMS_FN = _wms_function()
+    if scale is None:
+        scale = 1.0 / (syndromes.shape[0] * B.R * B.n)
+    return _WMS_FN.apply(w, g, B, syndromes, llr, etrue, ckpt, scale)
 
 
 class Logicals:
