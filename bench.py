@@ -52,10 +52,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--shots", type=int, default=1_000_000, help="shots per p per step per GPU")
+    ap.add_argument("--workload", default="bb144", choices=["bb144", "mixed", "learned"],
+                    help="bb144: the headline configuration; mixed: [[72]]/[[144]]/[[288]] in one "
+                         "persistent graph-captured launch vs plain per-code launches")
+    ap.add_argument("--shots", type=int, default=None,
+                    help="bb144: shots per p per step per GPU (default 1e6); mixed: shots per step (default 3e5)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=100, help="learned: training steps")
+    ap.add_argument("--train-batch", type=int, default=1024, help="learned: shots per training step")
     return ap.parse_args()
 
 
@@ -187,10 +193,204 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+MIXED = (("bb72", 8), ("bb144", 16), ("bb288", 32))
+MIXED_P = 0.05
+
+
+def run_mixed(args):
+    """[[72]], [[144]] and [[288]] shots 1:1:1 (R = 8 / 16 / 32), depolarizing
+    p = 0.05, X and Z decoded: one persistent, autotuned, graph-captured
+    mbbp_decode_mixed per step against one plain mbbp_decode per (code, type)
+    on the same syndromes (identical outputs, hence identical LER)."""
+    import torch
+
+    from paper_2605_14170_gb300 import mbbp
+    from paper_2605_14170_gb300.inputs import named_code
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    per_code = max(1, args.shots // 3)
+    entries = []  # (code, bases for X errors / Z errors, logicals)
+    for name, R in MIXED:
+        c = named_code(name)
+        entries.append((c, mbbp.mbbp_build_bases(c.HZ, R, SEED), mbbp.mbbp_build_bases(c.HX, R, SEED + 1),
+                        mbbp.mbbp_logicals_build(c.HZ, c.HX), mbbp.mbbp_logicals_build(c.HX, c.HZ)))
+    bases = [b for e in entries for b in (e[1], e[2])]
+    P = mbbp.mbbp_plan_create(bases)
+    pm = 2 * MIXED_P / 3
+    synd, llrs, errs = [], [], []
+    for c, BZ, BX, _, _ in entries:
+        n, W = c.n, (c.n + 31) // 32
+        ex = torch.empty((per_code, W), dtype=torch.int32, device=dev)
+        ez = torch.empty_like(ex)
+        errs.append((ex, ez))
+        l = torch.full((n,), float(np.log((1 - pm) / pm)), dtype=torch.float32, device=dev)
+        for B in (BZ, BX):
+            synd.append(torch.empty((per_code, B.m), dtype=torch.uint8, device=dev))
+            llrs.append(l)
+    ios, ws = mbbp.mixed_buffers(P, synd, llrs)
+
+    def sample(k):
+        for i, (c, BZ, BX, _, _) in enumerate(entries):
+            ex, ez = errs[i]
+            mbbp.mbbp_sample_errors(c.n, per_code, (k * 3 + i) * per_code, SEED, MIXED_P, mbbp.NOISE_DEPOLARIZING, ex, ez)
+            mbbp.mbbp_syndrome(BZ, ex, synd[2 * i])
+            mbbp.mbbp_syndrome(BX, ez, synd[2 * i + 1])
+
+    sample(0)
+    torch.cuda.synchronize()
+    tuned_ms = mbbp.mbbp_plan_autotune(P, ios, ITERS, ALPHA, mbbp.RULE_NMS, ws)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        mbbp.mbbp_decode_mixed(P, ios, ITERS, ALPHA, mbbp.RULE_NMS, ws, stream=side)
+        side.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            mbbp.mbbp_decode_mixed(P, ios, ITERS, ALPHA, mbbp.RULE_NMS, ws, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    plain_out = [mbbp.decode(B, s, l, ITERS, ALPHA) for B, s, l in zip(bases, synd, llrs)]
+    counts = torch.zeros((len(bases), 3), dtype=torch.int64, device=dev)
+    launches = {"mixed": 0, "plain": 0}
+
+    def step_mixed(k):
+        sample(k)
+        graph.replay()
+        for i, (_, _, _, LZ, LX) in enumerate(entries):
+            mbbp.mbbp_judge(LZ, errs[i][0], ios[2 * i]["e_hat"], None, counts[2 * i])
+            mbbp.mbbp_judge(LX, errs[i][1], ios[2 * i + 1]["e_hat"], None, counts[2 * i + 1])
+        launches["mixed"] = 9 + 1 + len(bases) + 6  # sample+syndrome, BP, FWS per entry, judge
+
+    def step_plain(k):
+        sample(k)
+        for j, (B, s, l) in enumerate(zip(bases, synd, llrs)):
+            o = plain_out[j]
+            mbbp.mbbp_decode(B, s, l, ITERS, ALPHA, mbbp.RULE_NMS, o["e_hat"], o["conv"], o["success"],
+                             o["workspace"], iters_run=o["iters"], selected=o["selected"])
+        launches["plain"] = 9 + 2 * len(bases)
+
+    def timed(fn):
+        for k in range(args.warmup):
+            fn(k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(args.steps):
+            fn(args.warmup + k)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    with ClockSampler(0) as clk:
+        ms_mixed = timed(step_mixed)
+    counts_mixed = counts.clone()
+    ms_plain = timed(step_plain)
+    # identical outputs on the last step's syndromes
+    same = all(torch.equal(x["e_hat"], o["e_hat"]) and torch.equal(x["iters"], o["iters"])
+               for x, o in zip(ios, plain_out))
+    shots = args.steps * 3 * per_code
+    info = mbbp.mbbp_plan_info(P)
+    cnt = counts_mixed.cpu().numpy()
+    names = [f"{c.name}:{t}" for c, *_ in entries for t in ("X", "Z")]
+    line = {
+        "metric": "decoded shots/s", "value": shots / (ms_mixed / 1e3), "unit": "shots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "mixed batch: [[72,12,6]] R=8, [[144,12,12]] R=16, [[288,12,18]] R=32, "
+                               "1:1:1, depolarizing p=0.05, X and Z decoded, 100 iters, one persistent "
+                               "autotuned graph-captured launch", "shots_per_step": 3 * per_code,
+                   "alpha": ALPHA},
+        "plain": {"value": shots / (ms_plain / 1e3), "unit": "shots/s", "ms_per_step": ms_plain / args.steps,
+                  "launches_per_step": launches["plain"]},
+        "speedup_vs_plain": ms_plain / ms_mixed,
+        "outputs_identical_to_plain": bool(same),
+        "ler": {nm: float(cnt[j, 1] + cnt[j, 2]) / (args.steps * per_code) for j, nm in enumerate(names)},
+        "plan": {"warps": info["warps"], "chunk": info["chunk"], "kind": info["kind"], "order": info["order"],
+                 "autotuned_ms": tuned_ms},
+        "gpu_launches": launches["mixed"] * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args):
+    """Learned-weight vs plain MBBP-LD on the length-882 GB code (R = 64,
+    100 iterations, depolarizing p in {0.02 .. 0.06}, X errors): WMS trained
+    on the GPU by the library's kernels (T = 25, checkpoint every 5,
+    validation-selected), then both decoders on the same fresh shots."""
+    import time as _time
+
+    import torch
+
+    from paper_2605_14170_gb300 import learn, mbbp
+    from paper_2605_14170_gb300.inputs import named_code
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    c = named_code("gb882")
+    B = mbbp.mbbp_build_bases(c.HZ, 64, SEED)
+    L = mbbp.mbbp_logicals_build(c.HZ, c.HX)
+    t0 = _time.time()
+    w, g, hist = learn.train_wms(B, 0.04, T=25, ckpt=5, batch=args.train_batch, steps=args.train_steps,
+                                 lr=1e-3, L=L, val_shots=10000, val_every=20, log_every=0)
+    torch.cuda.synchronize()
+    train_s = _time.time() - t0
+    shots = args.shots
+    res = {}
+    for p in (0.02, 0.03, 0.04, 0.05, 0.06):
+        res[str(p)] = learn.compare_ler(B, L, w, g, p, shots, ITERS, chunk=50000)
+    # throughput of the two decoders on one batch of p = 0.04 syndromes
+    n, W = c.n, (c.n + 31) // 32
+    ex = torch.empty((shots, W), dtype=torch.int32, device=dev)
+    ez = torch.empty_like(ex)
+    mbbp.mbbp_sample_errors(n, shots, 77_000_000_000, SEED, 0.04, mbbp.NOISE_DEPOLARIZING, ex, ez)
+    syn = torch.empty((shots, B.m), dtype=torch.uint8, device=dev)
+    mbbp.mbbp_syndrome(B, ex, syn)
+    pm = 2 * 0.04 / 3
+    llr = torch.full((n,), float(np.log((1 - pm) / pm)), dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_plain = timed(lambda: mbbp.decode(B, syn, llr, ITERS, ALPHA))
+    ms_learned = timed(lambda: mbbp.wms_decode(B, syn, llr, ITERS, w, g))
+    line = {
+        "metric": "decoded shots/s", "value": shots / (ms_learned / 1e3), "unit": "shots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "learned-weight vs plain MBBP-LD, length-882 GB code (seeded, k=4), R=64, "
+                               "100 iters, depolarizing X errors; WMS T=25, checkpoint 5, trained on GPU",
+                   "shots_per_p": shots, "train_batch": args.train_batch, "train_steps": args.train_steps},
+        "plain": {"value": shots / (ms_plain / 1e3), "unit": "shots/s", "ms_per_step": ms_plain},
+        "train_s": train_s,
+        "selected_step": min(hist, key=lambda h: (h[2] if h[2] is not None else 1 << 60))[0],
+        "ler": {p: {"plain": r["plain"]["ler"], "plain_ci95": r["plain"]["ci95"],
+                    "learned": r["learned"]["ler"], "learned_ci95": r["learned"]["ci95"]} for p, r in res.items()},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.shots is None:
+        args.shots = {"mixed": 300_000, "learned": 100_000}.get(args.workload, 1_000_000)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "mixed":
+        run_mixed(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
 
     import torch

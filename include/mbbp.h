@@ -264,7 +264,8 @@ mbbp_status mbbp_plan_info(const mbbp_plan* P, int32_t* warps, int32_t* chunk, i
  *   mn_e = min(LMAX, min_{other e' of c} |q^(t-1)_e'|),
  *   q^(t)_e = mu_v + sum_{other e' of v} m^(t)_e', m^(0) = 0, q^(0) = mu,
  * for t = 1..T (flooding, no early stop); loss of a (shot, representation):
- *   scale * sum_v BCE(sigmoid(-post_v), e_v), post = mu + sum_c m^(T).
+ *   scale * sum_v BCE(sigmoid(-post_v), e_v), post = mu + sum_c m^(T),
+ * or, with all_iters != 0, the mean of that over the posteriors of t = 1..T.
  * w and g are device float[R][T][E], E = the largest edge count of the
  * representations (mbbp_bases_info), edges numbered row by row of H^(t),
  * columns ascending. */
@@ -274,12 +275,14 @@ mbbp_status mbbp_plan_info(const mbbp_plan* P, int32_t* warps, int32_t* chunk, i
 size_t mbbp_wms_workspace_size(const mbbp_bases* B, int batch, int T, int ckpt);
 
 /* Forward pass.  syndromes, llr, llr_stride: as mbbp_decode.  etrue: device
- * uint8[batch*n] true errors or NULL; posterior: device float[batch*R*n]
+ * uint32[batch*W(n)] bit-packed true errors (as mbbp_sample_errors writes
+ * them) or NULL; posterior: device float[batch*R*n]
  * (needed by the backward pass); loss: device float[batch*R] or NULL (needs
  * etrue).  The workspace keeps the checkpoints for mbbp_wms_backward. */
 mbbp_status mbbp_wms_forward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
                              int llr_stride, int T, const float* w, const float* g, int ckpt,
-                             const uint8_t* etrue, float scale, float* posterior, float* loss,
+                             const uint32_t* etrue, float scale, int all_iters, float* posterior,
+                             float* loss,
                              void* workspace, size_t workspace_bytes, void* stream);
 
 /* Backward pass (hand-written adjoint): adds dL/dw and dL/dg (device
@@ -291,7 +294,8 @@ mbbp_status mbbp_wms_forward(const mbbp_bases* B, int batch, const uint8_t* synd
  * from their checkpoint.  Accumulation order varies (atomics). */
 mbbp_status mbbp_wms_backward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
                               int llr_stride, int T, const float* w, const float* g, int ckpt,
-                              const uint8_t* etrue, float scale, const float* posterior, float* gw,
+                              const uint32_t* etrue, float scale, int all_iters, const float* posterior,
+                              float* gw,
                               float* gg, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Algorithm 1 with WMS as the BP of every representation: the halting rule

@@ -108,9 +108,9 @@ def _load():
                 fn = getattr(lib, name)
                 fn.restype = C.c_double
             lib.or_wms_forward.argtypes = [u8p, C.c_int, C.c_int, u8p, f64p, C.c_int, f64p, f64p,
-                                           vp, C.c_double, vp]
+                                           vp, C.c_double, C.c_int, vp]
             lib.or_wms_backward.argtypes = [u8p, C.c_int, C.c_int, u8p, f64p, C.c_int, f64p, f64p,
-                                            u8p, C.c_double, f64p, f64p]
+                                            u8p, C.c_double, C.c_int, f64p, f64p]
             lib.or_judge.restype = None
             lib.or_judge.argtypes = [u8p, C.c_int, u8p, C.c_int, C.c_int, C.c_int,
                                      u8p, u8p, u8p]
@@ -273,10 +273,11 @@ def mbbp_decode(H, sets, synd, llr, iters: int, alpha: float,
     return out
 
 
-def wms_forward(Ht, st, mu, w, g, etrue=None, scale: float = 1.0):
+def wms_forward(Ht, st, mu, w, g, etrue=None, scale: float = 1.0, all_iters: bool = False):
     """Weighted min-sum on one representation, FP64 (see mbbp_oracle.c).
     w, g: [T, E] (edges row by row, columns ascending).  Returns
-    (loss, posterior) with loss = scale * sum_v BCE(sigmoid(-post_v), e_v)."""
+    (loss, posterior) with loss = scale * sum_v BCE(sigmoid(-post_v), e_v)
+    of the last iteration, or its mean over all iterations (all_iters)."""
     Ht, st = _u8(Ht), _u8(st)
     M, n = Ht.shape
     w = np.ascontiguousarray(w, dtype=np.float64)
@@ -284,11 +285,11 @@ def wms_forward(Ht, st, mu, w, g, etrue=None, scale: float = 1.0):
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     post = np.zeros(n)
     et = None if etrue is None else _u8(etrue)
-    L = _load().or_wms_forward(Ht, M, n, st, mu, w.shape[0], w, g, _ptr(et), scale, _ptr(post))
+    L = _load().or_wms_forward(Ht, M, n, st, mu, w.shape[0], w, g, _ptr(et), scale, int(all_iters), _ptr(post))
     return float(L), post
 
 
-def wms_backward(Ht, st, mu, w, g, etrue, scale: float = 1.0):
+def wms_backward(Ht, st, mu, w, g, etrue, scale: float = 1.0, all_iters: bool = False):
     """Adjoint of wms_forward: (loss, dL/dw [T, E], dL/dg [T, E])."""
     Ht, st, et = _u8(Ht), _u8(st), _u8(etrue)
     M, n = Ht.shape
@@ -297,7 +298,7 @@ def wms_backward(Ht, st, mu, w, g, etrue, scale: float = 1.0):
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     gw = np.zeros_like(w)
     gg = np.zeros_like(g)
-    L = _load().or_wms_backward(Ht, M, n, st, mu, w.shape[0], w, g, et, scale, gw, gg)
+    L = _load().or_wms_backward(Ht, M, n, st, mu, w.shape[0], w, g, et, scale, int(all_iters), gw, gg)
     return float(L), gw, gg
 
 

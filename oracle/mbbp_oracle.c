@@ -383,8 +383,9 @@ void or_judge(const uint8_t* Hc, int mc, const uint8_t* Ho, int mo, int n,
  *   q^(t)_e = mu_v + sum_{other e' of v} m^(t)_e' (ascending row order),
  * with m^(0) = 0, q^(0) = mu, for t = 1..T.  Edges are numbered row by row,
  * columns ascending; w and g are [T][E].  Loss of the item:
- *   L = scale * sum_v BCE(sigmoid(-post_v), e_v),  post = mu + sum_c m^(T).
- * Outputs post[n] and returns L. */
+ *   L = scale * sum_v BCE(sigmoid(-post_v), e_v),  post = mu + sum_c m^(T),
+ * or, with all_iters, the mean of that over the posteriors of t = 1..T.
+ * Outputs post[n] (of iteration T) and returns L. */
 static int or_wms_graph(const uint8_t* Ht, int M, int n, int** row_start, int** edge_col,
                         int** col_start, int** col_edges)
 {
@@ -461,7 +462,7 @@ static double or_bce_sigmoid_neg(double post, int e)
 
 double or_wms_forward(const uint8_t* Ht, int M, int n, const uint8_t* st, const double* mu,
                       int T, const double* w, const double* g, const uint8_t* etrue,
-                      double scale, double* post_out)
+                      double scale, int all_iters, double* post_out)
 {
     int *row_start, *edge_col, *col_start, *col_edges;
     int E = or_wms_graph(Ht, M, n, &row_start, &edge_col, &col_start, &col_edges);
@@ -472,16 +473,19 @@ double or_wms_forward(const uint8_t* Ht, int M, int n, const uint8_t* st, const 
     double* post = (double*)calloc((size_t)n + 1, sizeof(double));
     for (int k = 0; k < E; k++) q[k] = mu[edge_col[k]];
     for (int v = 0; v < n; v++) post[v] = mu[v];
+    double L = 0;
     for (int t = 0; t < T; t++) {
         or_wms_step(M, n, row_start, col_start, col_edges, edge_col, st, mu,
                     w + (size_t)t * E, g + (size_t)t * E, m_prev, q, m_new, q_new, post);
         double* tmp = m_prev; m_prev = m_new; m_new = tmp;
         tmp = q; q = q_new; q_new = tmp;
+        /* all_iters: the loss is the mean over t = 1..T of the BCE of post^(t) */
+        if (etrue && all_iters && t < T - 1)
+            for (int v = 0; v < n; v++) L += or_bce_sigmoid_neg(post[v], etrue[v] & 1) / T;
     }
-    double L = 0;
     for (int v = 0; v < n; v++) {
         if (post_out) post_out[v] = post[v];
-        if (etrue) L += or_bce_sigmoid_neg(post[v], etrue[v] & 1);
+        if (etrue) L += or_bce_sigmoid_neg(post[v], etrue[v] & 1) / (all_iters ? T : 1);
     }
     free(row_start); free(edge_col); free(col_start); free(col_edges);
     free(m_prev); free(m_new); free(q); free(q_new); free(post);
@@ -494,7 +498,7 @@ double or_wms_forward(const uint8_t* Ht, int M, int n, const uint8_t* st, const 
  * |q| is below LMAX; the derivative of the sign is 0.  Returns L. */
 double or_wms_backward(const uint8_t* Ht, int M, int n, const uint8_t* st, const double* mu,
                        int T, const double* w, const double* g, const uint8_t* etrue,
-                       double scale, double* gw, double* gg)
+                       double scale, int all_iters, double* gw, double* gg)
 {
     int *row_start, *edge_col, *col_start, *col_edges;
     int E = or_wms_graph(Ht, M, n, &row_start, &edge_col, &col_start, &col_edges);
@@ -509,15 +513,17 @@ double or_wms_backward(const uint8_t* Ht, int M, int n, const uint8_t* st, const
                     w + (size_t)t * E, g + (size_t)t * E, ms + (size_t)t * E,
                     qs + (size_t)t * E, ms + (size_t)(t + 1) * E, qs + (size_t)(t + 1) * E, post);
     double L = 0;
+    const double wt_loss = all_iters ? 1.0 / T : 1.0;  /* weight of one iteration's BCE */
     double* gm = (double*)calloc((size_t)E + 1, sizeof(double));   /* dL/dm^(t) */
     double* gm_prev = (double*)calloc((size_t)E + 1, sizeof(double));
     double* gq = (double*)calloc((size_t)E + 1, sizeof(double));   /* dL/dq^(t-1) */
+    double* pst = (double*)calloc((size_t)n + 1, sizeof(double));
     for (int v = 0; v < n; v++) {
         int e = etrue[v] & 1;
-        L += or_bce_sigmoid_neg(post[v], e);
+        L += or_bce_sigmoid_neg(post[v], e) * wt_loss;
         /* dBCE/dpost = e - sigmoid(-post) */
         double p = 1.0 / (1.0 + exp(post[v]));
-        double gp = scale * ((double)e - p);
+        double gp = scale * wt_loss * ((double)e - p);
         for (int i = col_start[v]; i < col_start[v + 1]; i++) gm[col_edges[i]] = gp;
     }
     for (int t = T; t >= 1; t--) {
@@ -559,9 +565,22 @@ double or_wms_backward(const uint8_t* Ht, int M, int n, const uint8_t* st, const
                 }
             }
         }
+        /* all_iters: the BCE of post^(t-1) (t - 1 >= 1) joins dL/dm^(t-1) */
+        if (all_iters && t >= 2) {
+            for (int v = 0; v < n; v++) {
+                double acc = mu[v];
+                for (int i = col_start[v]; i < col_start[v + 1]; i++) acc = acc + m_prev[col_edges[i]];
+                pst[v] = acc;
+                int e = etrue[v] & 1;
+                L += or_bce_sigmoid_neg(acc, e) * wt_loss;
+                double p = 1.0 / (1.0 + exp(acc));
+                double gp = scale * wt_loss * ((double)e - p);
+                for (int i = col_start[v]; i < col_start[v + 1]; i++) gm_prev[col_edges[i]] += gp;
+            }
+        }
         double* tmp = gm; gm = gm_prev; gm_prev = tmp;
     }
     free(row_start); free(edge_col); free(col_start); free(col_edges);
-    free(ms); free(qs); free(post); free(gm); free(gm_prev); free(gq);
+    free(ms); free(qs); free(post); free(gm); free(gm_prev); free(gq); free(pst);
     return scale * L;
 }

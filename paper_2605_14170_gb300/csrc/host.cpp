@@ -981,7 +981,8 @@ size_t mbbp_wms_workspace_size(const mbbp_bases* B, int batch, int T, int ckpt) 
 
 mbbp_status mbbp_wms_forward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
                              int llr_stride, int T, const float* w, const float* g, int ckpt,
-                             const uint8_t* etrue, float scale, float* posterior, float* loss,
+                             const uint32_t* etrue, float scale, int all_iters, float* posterior,
+                             float* loss,
                              void* workspace, size_t workspace_bytes, void* stream) {
     if (mbbp_status st = wms_check(B, batch, T, ckpt)) return st;
     if (batch == 0) return MBBP_OK;
@@ -1003,6 +1004,7 @@ mbbp_status mbbp_wms_forward(const mbbp_bases* B, int batch, const uint8_t* synd
     a.g = g;
     a.etrue = etrue;
     a.scale = scale;
+    a.all_iters = all_iters ? 1 : 0;
     a.post = posterior;
     a.loss = loss;
     a.counter = static_cast<unsigned long long*>(workspace);
@@ -1016,7 +1018,8 @@ mbbp_status mbbp_wms_forward(const mbbp_bases* B, int batch, const uint8_t* synd
 
 mbbp_status mbbp_wms_backward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
                               int llr_stride, int T, const float* w, const float* g, int ckpt,
-                              const uint8_t* etrue, float scale, const float* posterior, float* gw,
+                              const uint32_t* etrue, float scale, int all_iters, const float* posterior,
+                              float* gw,
                               float* gg, void* workspace, size_t workspace_bytes, void* stream) {
     if (mbbp_status st = wms_check(B, batch, T, ckpt)) return st;
     if (batch == 0) return MBBP_OK;
@@ -1037,6 +1040,7 @@ mbbp_status mbbp_wms_backward(const mbbp_bases* B, int batch, const uint8_t* syn
     a.g = g;
     a.etrue = etrue;
     a.scale = scale;
+    a.all_iters = all_iters ? 1 : 0;
     a.post = const_cast<float*>(posterior);
     a.gw = gw;
     a.gg = gg;

@@ -119,8 +119,9 @@ struct WmsArgs {
     int T, ckpt, nckpt, E;      // iterations, checkpoint interval, stored checkpoints, edges per row of w/g
     const float* w;             // [R][T][E]
     const float* g;             // [R][T][E]
-    const uint8_t* etrue;       // [batch][n] or null
+    const uint32_t* etrue;      // [batch][W] bit-packed true errors, or null
     float scale;
+    int all_iters;              // loss: mean BCE over all iterations instead of the last
     float* post;                // [batch][R][n]
     float* loss;                // [batch][R] or null
     float* ckpt_buf;            // [batch][R][nckpt][DC*MP]

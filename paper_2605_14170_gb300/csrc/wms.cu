@@ -6,7 +6,8 @@
 //   S_e = (-1)^{s_c} prod_{other e' of c} sign(q^(t-1)_e'),
 //   mn_e = min(LMAX, min_{other e' of c} |q^(t-1)_e'|),
 //   q^(t)_e = mu_v + sum_{other e' of v} m^(t)_e',  m^(0) = 0, q^(0) = mu.
-// Loss of an item: scale * sum_v BCE(sigmoid(-post_v), e_v), post = mu + sum m^(T).
+// Loss of an item: scale * sum_v BCE(sigmoid(-post_v), e_v), post = mu + sum m^(T),
+// or (all_iters) the mean of that over the posteriors of iterations 1..T.
 //
 // Kernels (one warp per (shot, representation), generic slot layout):
 //   wms_forward   T iterations, posterior, loss, a checkpoint of m every
@@ -156,6 +157,7 @@ wms_forward_kernel(const WmsArgs a) {
         __syncwarp();
         int K = 0;
         bool conv = false;
+        float lacc = 0.f;  // this lane's BCE of the posteriors of iterations 1..T-1 (all_iters)
         const int iters = a.decode ? a.iters : a.T;
         for (int it = 0;; ++it) {
             if (a.decode) {
@@ -189,9 +191,15 @@ wms_forward_kernel(const WmsArgs a) {
             if (a.decode) {
                 for (int v = lane; v < n; v += 32) eh[v] = (post[v] < 0.f) ? 1 : 0;
                 __syncwarp();
-            } else if (a.ckpt_buf && (it + 1) % a.ckpt == 0 && it + 1 < a.T) {
-                float* dst = a.ckpt_buf + ((size_t)item * a.nckpt + ((it + 1) / a.ckpt - 1)) * L.S;
-                for (int i = lane; i < L.S; i += 32) dst[i] = m[i];
+            } else {
+                if (a.ckpt_buf && (it + 1) % a.ckpt == 0 && it + 1 < a.T) {
+                    float* dst = a.ckpt_buf + ((size_t)item * a.nckpt + ((it + 1) / a.ckpt - 1)) * L.S;
+                    for (int i = lane; i < L.S; i += 32) dst[i] = m[i];
+                }
+                if (a.all_iters && a.etrue && a.loss && it + 1 < a.T) {
+                    for (int v = lane; v < n; v += 32)
+                        lacc += bce_neg_sigmoid(post[v], (int)((__ldg(a.etrue + (size_t)shot * W + (v >> 5)) >> (v & 31)) & 1u));
+                }
             }
         }
         if (a.post)
@@ -214,10 +222,11 @@ wms_forward_kernel(const WmsArgs a) {
         } else if (a.etrue && a.loss) {
             float acc = 0.f;
             for (int v = lane; v < n; v += 32)
-                acc += bce_neg_sigmoid(post[v], a.etrue[(size_t)shot * n + v] & 1);
+                acc += bce_neg_sigmoid(post[v], (int)((__ldg(a.etrue + (size_t)shot * W + (v >> 5)) >> (v & 31)) & 1u));
+            acc += lacc;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-            if (lane == 0) a.loss[item] = a.scale * acc;
+            if (lane == 0) a.loss[item] = a.scale * acc * (a.all_iters ? 1.0f / a.T : 1.0f);
         }
         __syncwarp();
     }
@@ -258,14 +267,16 @@ wms_backward_kernel(const WmsArgs a) {
             if (r < Mb) sb |= (uint32_t)(__ldg(sy + (__ldg(rinfo + r) & 0xffffu)) & 1u) << k;
         }
         for (int i = lane; i < L.S; i += 32) gm[i] = 0.0f;
+        const float lw = a.scale * (a.all_iters ? 1.0f / a.T : 1.0f);  // weight of one iteration's BCE
         __syncwarp();
-        // dL/dm^(T)_e = scale (e_v - sigmoid(-post_v)) on every edge of v
+        // dL/dm^(T)_e = lw (e_v - sigmoid(-post_v)) on every edge of v
         for (int p = lane; p < n; p += 32) {
             const uint2 d = __ldg(vd + p);
             const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
             const float pv = __ldg(a.post + item * n + v);
             const float sig = 1.0f / (1.0f + expf(pv));
-            const float gp = a.scale * ((float)(a.etrue[(size_t)shot * n + v] & 1) - sig);
+            const uint32_t ev = (__ldg(a.etrue + (size_t)shot * B.W + (v >> 5)) >> (v & 31)) & 1u;
+            const float gp = lw * ((float)ev - sig);
             for (int i = 0; i < deg; ++i) gm[__ldg(B.vslot + d.x + i)] = gp;
         }
         __syncwarp();
@@ -364,13 +375,21 @@ wms_backward_kernel(const WmsArgs a) {
                 if (t >= 2) {
                     for (int p = lane; p < n; p += 32) {
                         const uint2 d = __ldg(vd + p);
-                        const int deg = (int)(d.y >> 16);
+                        const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
                         const uint16_t* sl = B.vslot + d.x;
                         float G = 0.0f;
                         for (int i = 0; i < deg; ++i) G += gq[__ldg(sl + i)];
+                        // all_iters: the BCE of post^(t-1) joins dL/dm^(t-1)
+                        float gp = 0.0f;
+                        if (a.all_iters) {
+                            float acc = mu[v];
+                            for (int i = 0; i < deg; ++i) acc = __fadd_rn(acc, mprev[__ldg(sl + i)]);
+                            const uint32_t ev = (__ldg(a.etrue + (size_t)shot * B.W + (v >> 5)) >> (v & 31)) & 1u;
+                            gp = lw * ((float)ev - 1.0f / (1.0f + expf(acc)));
+                        }
                         for (int i = 0; i < deg; ++i) {
                             const int e = __ldg(sl + i);
-                            gmp[e] += G - gq[e];
+                            gmp[e] += G - gq[e] + gp;
                         }
                     }
                 }

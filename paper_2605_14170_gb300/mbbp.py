@@ -81,9 +81,9 @@ _sig = {
     "mbbp_plan_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "mbbp_wms_workspace_size": (C.c_size_t, [_vp, C.c_int, C.c_int, C.c_int]),
     "mbbp_wms_forward": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp,
-                                   C.c_float, _vp, _vp, _vp, C.c_size_t, _vp]),
+                                   C.c_float, C.c_int, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_wms_backward": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp,
-                                    C.c_float, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+                                    C.c_float, C.c_int, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_wms_decode": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp,
                                   _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_adam_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_size_t, C.c_float, C.c_float, C.c_float,
@@ -395,23 +395,23 @@ def _llr_stride(llr):
 
 
 def mbbp_wms_forward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, posterior, loss, workspace,
-                     stream=None) -> None:
+                     all_iters=False, stream=None) -> None:
     import torch
     _check(_lib.mbbp_wms_forward(
         B.handle, syndromes.shape[0], _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
         _llr_stride(llr), T, _dptr(w, torch.float32, "w"), _dptr(g, torch.float32, "g"), ckpt,
-        _dptr(etrue, torch.uint8, "etrue"), float(scale), _dptr(posterior, torch.float32, "posterior"),
+        _dptr(etrue, torch.int32, "etrue"), float(scale), int(all_iters), _dptr(posterior, torch.float32, "posterior"),
         _dptr(loss, torch.float32, "loss"), _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
         _stream(stream)), "mbbp_wms_forward")
 
 
 def mbbp_wms_backward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, posterior, gw, gg, workspace,
-                      stream=None) -> None:
+                      all_iters=False, stream=None) -> None:
     import torch
     _check(_lib.mbbp_wms_backward(
         B.handle, syndromes.shape[0], _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
         _llr_stride(llr), T, _dptr(w, torch.float32, "w"), _dptr(g, torch.float32, "g"), ckpt,
-        _dptr(etrue, torch.uint8, "etrue"), float(scale), _dptr(posterior, torch.float32, "posterior"),
+        _dptr(etrue, torch.int32, "etrue"), float(scale), int(all_iters), _dptr(posterior, torch.float32, "posterior"),
         _dptr(gw, torch.float32, "gw"), _dptr(gg, torch.float32, "gg"), _dptr(workspace, torch.uint8, "workspace"),
         workspace.numel(), _stream(stream)), "mbbp_wms_backward")
 
@@ -460,14 +460,14 @@ def _wms_function():
         kernel (mbbp_wms_backward) with checkpoints every `ckpt` iterations."""
 
         @staticmethod
-        def forward(ctx, w, g, B, syndromes, llr, etrue, ckpt, scale):
+        def forward(ctx, w, g, B, syndromes, llr, etrue, ckpt, scale, all_iters):
             T = w.shape[1]
             batch = syndromes.shape[0]
             post = torch.empty((batch, B.R, B.n), dtype=torch.float32, device=w.device)
             loss = torch.empty((batch, B.R), dtype=torch.float32, device=w.device)
             ws = torch.empty(mbbp_wms_workspace_size(B, batch, T, ckpt), dtype=torch.uint8, device=w.device)
-            mbbp_wms_forward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, post, loss, ws)
-            ctx.B, ctx.ckpt, ctx.scale = B, ckpt, scale
+            mbbp_wms_forward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, post, loss, ws, all_iters=all_iters)
+            ctx.B, ctx.ckpt, ctx.scale, ctx.all_iters = B, ckpt, scale, all_iters
             ctx.save_for_backward(w, g, syndromes, llr, etrue, post, ws)
             return loss.sum()
 
@@ -476,8 +476,9 @@ def _wms_function():
             w, g, syndromes, llr, etrue, post, ws = ctx.saved_tensors
             gw = torch.zeros_like(w)
             gg = torch.zeros_like(g)
-            mbbp_wms_backward(ctx.B, syndromes, llr, w.shape[1], w, g, ctx.ckpt, etrue, ctx.scale, post, gw, gg, ws)
-            return gw * grad_out, gg * grad_out, None, None, None, None, None, None
+            mbbp_wms_backward(ctx.B, syndromes, llr, w.shape[1], w, g, ctx.ckpt, etrue, ctx.scale, post, gw, gg, ws,
+                              all_iters=ctx.all_iters)
+            return gw * grad_out, gg * grad_out, None, None, None, None, None, None, None
 
     return WMSLoss
 
@@ -485,15 +486,16 @@ def _wms_function():
 _WMS_FN = None
 
 
-def wms_loss(w, g, B, syndromes, llr, etrue, ckpt: int = 5, scale: float | None = None):
+def wms_loss(w, g, B, syndromes, llr, etrue, ckpt: int = 5, scale: float | None = None, all_iters: bool = False):
     """Differentiable WMS loss (mean BCE over shots, representations and
-    variables unless ``scale`` is given)."""
+    variables unless ``scale`` is given; with ``all_iters`` also over the
+    iterations).  etrue: bit-packed true errors (int32 words)."""
     global _WMS_FN
     if _WMS_FN is None:
         _WMS_FN = _wms_function()
     if scale is None:
         scale = 1.0 / (syndromes.shape[0] * B.R * B.n)
-    return _WMS_FN.apply(w, g, B, syndromes, llr, etrue, ckpt, scale)
+    return _WMS_FN.apply(w, g, B, syndromes, llr, etrue, ckpt, scale, all_iters)
 
 
 class Logicals:

@@ -34,7 +34,7 @@ def _setup(code="bb72", R=2, shots=12, T=8, seed=1, p=0.07):
     dev = torch.device("cuda:0")
     t = {"s": torch.from_numpy(s).to(dev), "mu": torch.from_numpy(mu.astype(np.float32)).to(dev),
          "w": torch.from_numpy(w.astype(np.float32)).to(dev), "g": torch.from_numpy(g.astype(np.float32)).to(dev),
-         "e": torch.from_numpy(ex).to(dev)}
+         "e": torch.from_numpy(mbbp.pack_bits(ex)).to(dev)}
     return H, B, s, ex, mu, w, g, t
 
 
@@ -70,20 +70,21 @@ def test_wms_forward_matches_fp64_oracle():
     post = torch.empty((20, B.R, 72), dtype=torch.float32, device="cuda")
     loss = torch.empty((20, B.R), dtype=torch.float32, device="cuda")
     ws = torch.empty(mbbp.mbbp_wms_workspace_size(B, 20, 8, 3), dtype=torch.uint8, device="cuda")
-    mbbp.mbbp_wms_forward(B, t["s"], t["mu"], 8, t["w"], t["g"], 3, t["e"], scale, post, loss, ws)
+    mbbp.mbbp_wms_forward(B, t["s"], t["mu"], 8, t["w"], t["g"], 3, t["e"], scale, post, loss, ws, all_iters=True)
     torch.cuda.synchronize()
     post, loss = post.cpu().numpy(), loss.cpu().numpy()
     mu32 = mu.astype(np.float32).astype(np.float64)
     for shot in range(20):
         for b in range(B.R):
             Ht, st, wb, gb, _ = _oracle_item(H, B, s, mu32, w.astype(np.float32), g.astype(np.float32), ex, shot, b, scale)
-            L, p64 = oracle.wms_forward(Ht, st, mu32, wb, gb, ex[shot], scale)
+            L, p64 = oracle.wms_forward(Ht, st, mu32, wb, gb, ex[shot], scale, all_iters=True)
             err = np.abs(post[shot, b] - p64) / np.maximum(np.abs(p64), 1.0)
             assert err.max() <= 1e-4, (shot, b, err.max())
             assert loss[shot, b] == pytest.approx(L, rel=1e-4)
 
 
-def test_wms_gradients_match_oracle_adjoint_and_finite_differences():
+@pytest.mark.parametrize("all_iters", [False, True])
+def test_wms_gradients_match_oracle_adjoint_and_finite_differences(all_iters):
     import torch
     from paper_2605_14170_gb300 import mbbp
     shots, T = 12, 8
@@ -95,16 +96,18 @@ def test_wms_gradients_match_oracle_adjoint_and_finite_differences():
     for shot in range(shots):
         for b in range(B.R):
             Ht, st, wb, gb, Eb = _oracle_item(H, B, s, mu32, w32, g32, ex, shot, b, scale)
-            _, gwb, ggb = oracle.wms_backward(Ht, st, mu32, wb, gb, ex[shot], scale)
+            _, gwb, ggb = oracle.wms_backward(Ht, st, mu32, wb, gb, ex[shot], scale, all_iters=all_iters)
             gw_ref[b][:, :Eb] += gwb
             gg_ref[b][:, :Eb] += ggb
             items.append((shot, b, Ht, st, Eb))
     post = torch.empty((shots, B.R, 72), dtype=torch.float32, device="cuda")
     ws = torch.empty(mbbp.mbbp_wms_workspace_size(B, shots, T, 3), dtype=torch.uint8, device="cuda")
-    mbbp.mbbp_wms_forward(B, t["s"], t["mu"], T, t["w"], t["g"], 3, t["e"], scale, post, None, ws)
+    mbbp.mbbp_wms_forward(B, t["s"], t["mu"], T, t["w"], t["g"], 3, t["e"], scale, post, None, ws,
+                          all_iters=all_iters)
     gw = torch.zeros_like(t["w"])
     gg = torch.zeros_like(t["g"])
-    mbbp.mbbp_wms_backward(B, t["s"], t["mu"], T, t["w"], t["g"], 3, t["e"], scale, post, gw, gg, ws)
+    mbbp.mbbp_wms_backward(B, t["s"], t["mu"], T, t["w"], t["g"], 3, t["e"], scale, post, gw, gg, ws,
+                           all_iters=all_iters)
     torch.cuda.synchronize()
     gw, gg = gw.cpu().numpy().astype(np.float64), gg.cpu().numpy().astype(np.float64)
     for got, ref in ((gw, gw_ref), (gg, gg_ref)):
@@ -118,7 +121,8 @@ def test_wms_gradients_match_oracle_adjoint_and_finite_differences():
     def total(wx, gx):
         tot = 0.0
         for shot, b, Ht, st, Eb in items:
-            L, _ = oracle.wms_forward(Ht, st, mu32, wx[b][:, :Eb], gx[b][:, :Eb], ex[shot], scale)
+            L, _ = oracle.wms_forward(Ht, st, mu32, wx[b][:, :Eb], gx[b][:, :Eb], ex[shot], scale,
+                                      all_iters=all_iters)
             tot += L
         return tot
 
@@ -168,15 +172,15 @@ def test_autograd_function_and_adam():
     H, B, s, ex, mu, w, g, t = _setup(shots=shots, T=T, seed=5)
     wt = t["w"].clone().requires_grad_(True)
     gt = t["g"].clone().requires_grad_(True)
-    loss = mbbp.wms_loss(wt, gt, B, t["s"], t["mu"], t["e"], ckpt=2)
+    loss = mbbp.wms_loss(wt, gt, B, t["s"], t["mu"], t["e"], ckpt=2, all_iters=True)
     loss.backward()
     post = torch.empty((shots, B.R, 72), dtype=torch.float32, device="cuda")
     ws = torch.empty(mbbp.mbbp_wms_workspace_size(B, shots, T, 2), dtype=torch.uint8, device="cuda")
     scale = 1.0 / (shots * B.R * 72)
-    mbbp.mbbp_wms_forward(B, t["s"], t["mu"], T, t["w"], t["g"], 2, t["e"], scale, post, None, ws)
+    mbbp.mbbp_wms_forward(B, t["s"], t["mu"], T, t["w"], t["g"], 2, t["e"], scale, post, None, ws, all_iters=True)
     gw = torch.zeros_like(t["w"])
     gg = torch.zeros_like(t["g"])
-    mbbp.mbbp_wms_backward(B, t["s"], t["mu"], T, t["w"], t["g"], 2, t["e"], scale, post, gw, gg, ws)
+    mbbp.mbbp_wms_backward(B, t["s"], t["mu"], T, t["w"], t["g"], 2, t["e"], scale, post, gw, gg, ws, all_iters=True)
     torch.testing.assert_close(wt.grad, gw, rtol=1e-5, atol=1e-8)
     torch.testing.assert_close(gt.grad, gg, rtol=1e-5, atol=1e-8)
     # Adam against its definition (Kingma & Ba), clamped to [lo, hi]

@@ -65,11 +65,11 @@ def _random_point(seed, T=6):
     return Ht, st, mu, w, g, e
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_adjoint_matches_finite_differences(seed):
+@pytest.mark.parametrize("seed,all_iters", [(1, False), (2, False), (3, True), (4, True)])
+def test_adjoint_matches_finite_differences(seed, all_iters):
     Ht, st, mu, w, g, e = _random_point(seed)
-    L, gw, gg = oracle.wms_backward(Ht, st, mu, w, g, e, scale=1.0 / 72)
-    L2, _ = oracle.wms_forward(Ht, st, mu, w, g, e, scale=1.0 / 72)
+    L, gw, gg = oracle.wms_backward(Ht, st, mu, w, g, e, scale=1.0 / 72, all_iters=all_iters)
+    L2, _ = oracle.wms_forward(Ht, st, mu, w, g, e, scale=1.0 / 72, all_iters=all_iters)
     assert L == pytest.approx(L2, rel=1e-14)
     rng = np.random.default_rng(seed)
     h = 1e-6
@@ -82,13 +82,13 @@ def test_adjoint_matches_finite_differences(seed):
             Pp[t, k] += h
             Pm[t, k] -= h
             args = (Pp, g) if P is w else (w, Pp)
-            Lp, _ = oracle.wms_forward(Ht, st, mu, *args, e, scale=1.0 / 72)
+            Lp, _ = oracle.wms_forward(Ht, st, mu, *args, e, scale=1.0 / 72, all_iters=all_iters)
             args = (Pm, g) if P is w else (w, Pm)
-            Lm, _ = oracle.wms_forward(Ht, st, mu, *args, e, scale=1.0 / 72)
+            Lm, _ = oracle.wms_forward(Ht, st, mu, *args, e, scale=1.0 / 72, all_iters=all_iters)
             fd = (Lp - Lm) / (2 * h)
             # a kink (min or sign switching inside [-h, h]) makes the central
             # difference disagree with both one-sided slopes; skip those points
-            L0, _ = oracle.wms_forward(Ht, st, mu, w, g, e, scale=1.0 / 72)
+            L0, _ = oracle.wms_forward(Ht, st, mu, w, g, e, scale=1.0 / 72, all_iters=all_iters)
             right, left = (Lp - L0) / h, (L0 - Lm) / h
             if abs(right - left) > 1e-4 * max(abs(right), abs(left), 1e-8):
                 continue
