@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--train-steps", type=int, default=100, help="learned: training steps")
-    ap.add_argument("--train-batch", type=int, default=1024, help="learned: shots per training step")
+    ap.add_argument("--train-batch", type=int, default=512, help="learned: shots per training step")
     return ap.parse_args()
 
 

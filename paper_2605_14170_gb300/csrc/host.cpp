@@ -976,8 +976,19 @@ mbbp_status wms_check(const mbbp_bases* B, int batch, int T, int ckpt) {
 size_t mbbp_wms_workspace_size(const mbbp_bases* B, int batch, int T, int ckpt) {
     if (!B || batch < 0 || T < 1 || ckpt < 1) return 0;
     const size_t nckpt = (size_t)((T - 1) / ckpt);
-    return 256 + align256((size_t)batch * B->R * nckpt * B->dev.DC * B->MP * 4);
+    const size_t S = (size_t)B->dev.DC * B->MP;
+    return 256 + align256((size_t)batch * B->R * nckpt * S * 4) +
+           align256((size_t)kWmsMaxWarps * ckpt * S * 4);
 }
+
+namespace {
+float* wms_seg_buf(const mbbp_bases* B, int batch, int T, int ckpt, void* workspace) {
+    const size_t nckpt = (size_t)((T - 1) / ckpt);
+    const size_t S = (size_t)B->dev.DC * B->MP;
+    return reinterpret_cast<float*>(static_cast<char*>(workspace) + 256 +
+                                    align256((size_t)batch * B->R * nckpt * S * 4));
+}
+}  // namespace
 
 mbbp_status mbbp_wms_forward(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
                              int llr_stride, int T, const float* w, const float* g, int ckpt,
@@ -1044,6 +1055,7 @@ mbbp_status mbbp_wms_backward(const mbbp_bases* B, int batch, const uint8_t* syn
     a.post = const_cast<float*>(posterior);
     a.gw = gw;
     a.gg = gg;
+    a.seg_buf = wms_seg_buf(B, batch, T, ckpt, workspace);
     a.counter = static_cast<unsigned long long*>(workspace);
     a.ckpt_buf = a.nckpt ? reinterpret_cast<float*>(static_cast<char*>(workspace) + 256) : nullptr;
     a.total_items = (unsigned long long)batch * B->R;

@@ -125,6 +125,7 @@ struct WmsArgs {
     float* post;                // [batch][R][n]
     float* loss;                // [batch][R] or null
     float* ckpt_buf;            // [batch][R][nckpt][DC*MP]
+    float* seg_buf;             // backward: [kWmsMaxWarps][ckpt][DC*MP], one segment per warp
     float* gw;                  // [R][T][E]
     float* gg;
     int decode, iters;          // decode mode: halting rule, candidates
@@ -134,6 +135,7 @@ struct WmsArgs {
     unsigned long long* counter;
     unsigned long long total_items;
 };
+constexpr int kWmsMaxWarps = 152 * 16;  // warps of the backward grid (segment buffers)
 cudaError_t launch_wms(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count);
 cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, size_t count, float lr, float b1,
                         float b2, float eps, int step, float lo, float hi, cudaStream_t s);

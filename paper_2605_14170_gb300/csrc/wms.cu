@@ -40,8 +40,9 @@ __host__ __device__ inline WmsLayout wms_layout(int DC, int MP, int n, int ckpt)
     L.ehpad = (n + 1 + 15) & ~15;
     // forward: m, q (S each), mu, post (npad each), hard decision bytes
     L.fwd_bytes = (size_t)(2 * L.S + 2 * L.npad) * 4 + L.ehpad;
-    // backward: ckpt + 1 states of m, q, gm, gm_prev, gq (S each), mu (npad, with room for one more)
-    L.bwd_bytes = (size_t)((ckpt + 1) * L.S + 4 * L.S + 2 * L.npad) * 4;
+    // backward: q, gm, gm_prev, gq (S each), mu (npad); the segment's states
+    // live in a per-warp global buffer of ckpt * S floats
+    L.bwd_bytes = (size_t)(4 * L.S + L.npad) * 4;
     return L;
 }
 
@@ -241,8 +242,9 @@ wms_backward_kernel(const WmsArgs a) {
     const int warp = threadIdx.x >> 5;
     const int MP = B.MP, n = B.n, m_rows = B.m, R = B.R;
     const WmsLayout L = wms_layout(DC, MP, n, a.ckpt);
-    float* states = reinterpret_cast<float*>(smem + warp * L.bwd_bytes);  // [ckpt + 1][S]
-    float* q = states + (size_t)(a.ckpt + 1) * L.S;
+    const size_t gwarp = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    float* states = a.seg_buf + gwarp * (size_t)a.ckpt * L.S;  // [ckpt][S], this warp's
+    float* q = reinterpret_cast<float*>(smem + warp * L.bwd_bytes);
     float* gm = q + L.S;
     float* gmp = gm + L.S;
     float* gq = gmp + L.S;
@@ -431,6 +433,10 @@ cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm
     unsigned long long want = (a.total_items + warps - 1) / warps;
     unsigned long long grid = (unsigned long long)per_sm * sm_count;
     if (want < grid) grid = want;
+    if (backward) {  // one segment buffer per warp: at most kWmsMaxWarps warps
+        const unsigned long long cap = kWmsMaxWarps / warps;
+        if (grid > cap) grid = cap;
+    }
     if (backward)
         wms_backward_kernel<K, K><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     else
