@@ -15,8 +15,11 @@ Functions and the passages they follow:
 ``subtrees``               Algorithm 2, maximal subtrees
 ``permutation``            root orders pi_j (Section III-A)
 ``collect_subtrees``       the collection T over several orders (Section III-A)
-``bp``                     syndrome BP on one representation (Section II-B)
+``bp``                     syndrome BP on one representation (Section II-B),
+                           flooding or serial schedule
 ``fws``                    Frequency-Weighted Scoring (Section III-B)
+``lms``                    least-metric selection of classical MBBP (III-A)
+``random_sets``            random augmentation of Table II
 ``mbbp_decode``            Algorithm 1 over a batch of syndromes
 ``judge``                  logical-error test by GF(2) rank
 ``wms_forward``            weighted min-sum, FP64 (a reading of Section II-B)
@@ -97,12 +100,18 @@ def _load():
                 fn.argtypes = [u8p, C.c_int, C.c_int, u8p, fp, C.c_int, real,
                                C.c_int, C.c_int, u8p, C.POINTER(C.c_int),
                                C.POINTER(C.c_int), vp, vp]
+            for name, fp, real in (("or_bp_serial_one_f64", f64p, C.c_double),
+                                   ("or_bp_serial_one_f32", f32p, C.c_float)):
+                fn = getattr(lib, name)
+                fn.restype = None
+                fn.argtypes = [u8p, C.c_int, C.c_int, u8p, fp, C.c_int, real, C.c_int, C.c_int,
+                               u8p, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
             for name, fp, real in (("or_mbbp_decode_f64", f64p, C.c_double),
                                    ("or_mbbp_decode_f32", f32p, C.c_float)):
                 fn = getattr(lib, name)
                 fn.restype = None
                 fn.argtypes = [u8p, C.c_int, C.c_int, C.c_int, i32p, i32p,
-                               C.c_int, u8p, fp, C.c_int, C.c_int, real, C.c_int,
+                               C.c_int, u8p, fp, C.c_int, C.c_int, real, C.c_int, C.c_int, C.c_int,
                                u8p, u8p, vp, u8p, vp, vp, vp]
             for name in ("or_wms_forward", "or_wms_backward"):
                 fn = getattr(lib, name)
@@ -111,6 +120,10 @@ def _load():
                                            vp, C.c_double, C.c_int, vp]
             lib.or_wms_backward.argtypes = [u8p, C.c_int, C.c_int, u8p, f64p, C.c_int, f64p, f64p,
                                             u8p, C.c_double, C.c_int, f64p, f64p]
+            lib.or_lms.restype = C.c_int
+            lib.or_lms.argtypes = [u8p, u8p, C.c_int, C.c_int, f32p, u8p, C.POINTER(C.c_int)]
+            lib.or_random_sets.restype = None
+            lib.or_random_sets.argtypes = [C.c_int, C.c_int, i32p, C.c_uint64, i32p, i32p]
             lib.or_judge.restype = None
             lib.or_judge.argtypes = [u8p, C.c_int, u8p, C.c_int, C.c_int, C.c_int,
                                      u8p, u8p, u8p]
@@ -206,16 +219,26 @@ def _sets_arrays(sets):
 
 
 def bp(Ht, st, mu, iters: int, alpha: float, rule: int = RULE_NMS,
-       early_stop: bool = True, precision: str = "f64", want_c2v: bool = False):
-    """BP on one representation.  Returns dict(ehat, conv, K, post[, c2v])."""
+       early_stop: bool = True, precision: str = "f64", want_c2v: bool = False,
+       schedule: int = 0):
+    """BP on one representation.  Returns dict(ehat, conv, K, post[, c2v]).
+    schedule 0: flooding; 1: serial (layer-major check order, no c2v
+    output)."""
     Ht, st = _u8(Ht), _u8(st)
     M, n = Ht.shape
     dt = np.float64 if precision == "f64" else np.float32
     mu = np.ascontiguousarray(mu, dtype=dt)
     ehat = np.zeros(n, np.uint8)
     post = np.zeros(n, dt)
-    c2v = np.zeros((M, n), dt) if want_c2v else None
     conv, K = C.c_int(0), C.c_int(0)
+    if schedule == 1:
+        if want_c2v:
+            raise ValueError("serial schedule: no c2v output")
+        fn = _load().or_bp_serial_one_f64 if precision == "f64" else _load().or_bp_serial_one_f32
+        fn(Ht, M, n, st, mu, iters, alpha, rule, int(early_stop), ehat, C.byref(conv), C.byref(K),
+           _ptr(post))
+        return {"ehat": ehat, "conv": bool(conv.value), "K": int(K.value), "post": post}
+    c2v = np.zeros((M, n), dt) if want_c2v else None
     fn = _load().or_bp_one_f64 if precision == "f64" else _load().or_bp_one_f32
     fn(Ht, M, n, st, mu, iters, alpha, rule, int(early_stop), ehat,
        C.byref(conv), C.byref(K), _ptr(post), _ptr(c2v))
@@ -237,8 +260,35 @@ def fws(cand, conv):
     return ehat, bool(ok), int(sel.value)
 
 
+def lms(cand, conv, mu):
+    """Least-metric selection over (R, n) candidates: (ehat, success, index)."""
+    cand, conv = _u8(cand), _u8(conv)
+    R, n = cand.shape
+    ehat = np.zeros(n, np.uint8)
+    sel = C.c_int(-1)
+    ok = _load().or_lms(cand, conv, R, n, np.ascontiguousarray(mu, dtype=np.float32), ehat, C.byref(sel))
+    return ehat, bool(ok), int(sel.value)
+
+
+def random_sets(m: int, sizes, seed: int):
+    """Random augmentation of Table II: len(sizes) sets of distinct random rows."""
+    sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+    R = len(sizes)
+    ptr = np.zeros(R + 1, np.int32)
+    rows = np.zeros(max(int(sizes.sum()), 1), np.int32)
+    _load().or_random_sets(m, R, sizes, seed, ptr, rows)
+    return [rows[ptr[t]:ptr[t + 1]].copy() for t in range(R)]
+
+
+SCHEDULE_FLOODING = 0
+SCHEDULE_SERIAL = 1
+DECISION_FWS = 0
+DECISION_LMS = 1
+
+
 def mbbp_decode(H, sets, synd, llr, iters: int, alpha: float,
-                rule: int = RULE_NMS, precision: str = "f64", want_post: bool = False):
+                rule: int = RULE_NMS, precision: str = "f64", want_post: bool = False,
+                schedule: int = SCHEDULE_FLOODING, decision: int = DECISION_FWS):
     """Algorithm 1 for a batch: H (m, n); sets = list of R row arrays (H_t);
     synd (batch, m); llr (n,) shared or (batch, n) per shot.
 
@@ -264,7 +314,7 @@ def mbbp_decode(H, sets, synd, llr, iters: int, alpha: float,
     post = np.zeros((batch, R, n), dt) if want_post else None
     fn = _load().or_mbbp_decode_f64 if precision == "f64" else _load().or_mbbp_decode_f32
     fn(H, m, n, R, set_ptr, set_rows, batch, synd if synd.size else np.zeros(1, np.uint8),
-       llr, stride, iters, alpha, rule, out["ehat"] if batch else np.zeros(1, np.uint8),
+       llr, stride, iters, alpha, rule, schedule, decision, out["ehat"] if batch else np.zeros(1, np.uint8),
        out["conv"] if out["conv"].size else np.zeros(1, np.uint8), _ptr(out["iters"]),
        out["success"] if batch else np.zeros(1, np.uint8), _ptr(out["selected"]),
        _ptr(out["cand"]), _ptr(post))

@@ -297,28 +297,58 @@ int or_fws(const uint8_t* cand, const uint8_t* conv, int R, int n,
     return 1;
 }
 
+/* ---------------------------------------------------- LMS, random sets -- */
+
+/* Least-metric selector of classical MBBP (Section III-A): among the
+ * converged candidates the most likely one under the channel, i.e. the
+ * smallest sum_i mu_i e_i (for an i.i.d. channel the smallest weight).  The
+ * metric is a float sum in ascending i (the precision of the GPU path, which
+ * takes the same decision); ties go to the first candidate.  Returns 1 on
+ * success, 0 (and e = 0) when no candidate converged. */
+int or_lms(const uint8_t* cand, const uint8_t* conv, int R, int n, const float* mu,
+           uint8_t* ehat, int* selected)
+{
+    int best = -1;
+    float best_m = 0.0f;
+    for (int a = 0; a < R; a++) {
+        if (!conv[a]) continue;
+        float mt = 0.0f;
+        for (int v = 0; v < n; v++)
+            if (cand[(size_t)a * n + v]) mt = mt + mu[v];
+        if (best < 0 || mt < best_m) { best = a; best_m = mt; }
+    }
+    if (selected) *selected = best;
+    if (best < 0) { memset(ehat, 0, (size_t)n); return 0; }
+    memcpy(ehat, cand + (size_t)best * n, (size_t)n);
+    return 1;
+}
+
 /* ------------------------------------------------------------------- BP -- */
 
 #define REAL double
 #define BP_FN or_bp_f64
+#define BPS_FN or_bp_serial_f64
 #define DECODE_FN or_mbbp_decode_f64
 #define FABS fabs
 #define PHI or_phi64
 #include "bp_body.inc"
 #undef REAL
 #undef BP_FN
+#undef BPS_FN
 #undef DECODE_FN
 #undef FABS
 #undef PHI
 
 #define REAL float
 #define BP_FN or_bp_f32
+#define BPS_FN or_bp_serial_f32
 #define DECODE_FN or_mbbp_decode_f32
 #define FABS fabsf
 #define PHI or_phi32
 #include "bp_body.inc"
 #undef REAL
 #undef BP_FN
+#undef BPS_FN
 #undef DECODE_FN
 #undef FABS
 #undef PHI
@@ -338,6 +368,20 @@ void or_bp_one_f32(const uint8_t* Ht, int M, int n, const uint8_t* st,
                    float* post, float* c2v)
 {
     or_bp_f32(Ht, M, n, st, mu, iters, alpha, rule, early_stop, ehat, conv, K, post, c2v);
+}
+
+void or_bp_serial_one_f64(const uint8_t* Ht, int M, int n, const uint8_t* st,
+                          const double* mu, int iters, double alpha, int rule, int early_stop,
+                          uint8_t* ehat, int* conv, int* K, double* post)
+{
+    or_bp_serial_f64(Ht, M, n, st, mu, iters, alpha, rule, early_stop, ehat, conv, K, post);
+}
+
+void or_bp_serial_one_f32(const uint8_t* Ht, int M, int n, const uint8_t* st,
+                          const float* mu, int iters, float alpha, int rule, int early_stop,
+                          uint8_t* ehat, int* conv, int* K, float* post)
+{
+    or_bp_serial_f32(Ht, M, n, st, mu, iters, alpha, rule, early_stop, ehat, conv, K, post);
 }
 
 /* ---------------------------------------------------------------- judge -- */
@@ -583,4 +627,31 @@ double or_wms_backward(const uint8_t* Ht, int M, int n, const uint8_t* st, const
     free(row_start); free(edge_col); free(col_start); free(col_edges);
     free(ms); free(qs); free(post); free(gm); free(gm_prev); free(gq); free(pst);
     return scale * L;
+}
+
+/* Random augmentation, the comparison of Table II: representation t keeps
+ * the number of extra rows of subtree t, sizes[t], but draws them as
+ * distinct uniformly random rows of H.  Draw for representation t: a
+ * Fisher-Yates shuffle (i = m-1 down to 1, swap with x mod (i+1), x the
+ * outputs of splitmix64 seeded with seed XOR (t + 1)) of 0..m-1, first
+ * sizes[t] entries.  set_ptr[R+1] / set_rows as or_collect_subtrees. */
+void or_random_sets(int m, int R, const int32_t* sizes, uint64_t seed, int32_t* set_ptr,
+                    int32_t* set_rows)
+{
+    int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    set_ptr[0] = 0;
+    for (int t = 0; t < R; t++) {
+        for (int i = 0; i < m; i++) perm[i] = i;
+        uint64_t state = seed ^ (uint64_t)(t + 1);
+        uint64_t draw = 1;
+        for (int i = m - 1; i >= 1; i--) {
+            uint64_t x = or_splitmix64_at(state, draw++);
+            int k = (int)(x % (uint64_t)(i + 1));
+            int32_t tmp = perm[i]; perm[i] = perm[k]; perm[k] = tmp;
+        }
+        int len = sizes[t] < m ? sizes[t] : m;
+        for (int i = 0; i < len; i++) set_rows[set_ptr[t] + i] = perm[i];
+        set_ptr[t + 1] = set_ptr[t] + len;
+    }
+    free(perm);
 }

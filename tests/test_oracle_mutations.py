@@ -53,6 +53,29 @@ def pins_hold():
         return False
     if oracle.fws(c(["011100", "100000", "011100"]), [1, 1, 1])[2] != 0:
         return False
+    # serial schedule: worked examples (Section II-B)
+    H3 = np.array([[1, 1, 0, 0], [0, 1, 1, 0], [0, 0, 1, 1]], np.uint8)
+    r = oracle.bp(H3, np.array([0, 1, 0], np.uint8), np.array([1.0, -2.0, 3.0, 0.5]), 1, 1.0,
+                  oracle.RULE_NMS, early_stop=False, schedule=oracle.SCHEDULE_SERIAL)
+    if not np.array_equal(r["post"], [-1.0, -4.5, 4.5, 3.5]):
+        return False
+    for trial in range(3):
+        rng = np.random.default_rng(300 + trial)
+        Ht = random_tree(rng)
+        s = rng.integers(0, 2, Ht.shape[0]).astype(np.uint8)
+        mu = rng.uniform(-1.0, 3.0, Ht.shape[1])
+        lr, mc = brute_force(Ht, s, mu)
+        for rule, want in ((oracle.RULE_SP, lr), (oracle.RULE_NMS, mc)):
+            r = oracle.bp(Ht, s, mu, 2 * Ht.shape[1], 1.0, rule, early_stop=False,
+                          schedule=oracle.SCHEDULE_SERIAL)
+            if not np.allclose(r["post"], want, atol=1e-9):
+                return False
+    # LMS hand lists (Section III-A)
+    mu6 = np.array([1.0, -2.0, 3.0, 4.0, 5.0, 6.0], np.float32)
+    if oracle.lms(c(["001000", "010000", "100000"]), [1, 1, 1], mu6)[2] != 1:
+        return False
+    if oracle.lms(c(["001000", "000100", "001000"]), [1, 1, 1], np.abs(mu6) * 0 + 1)[2] != 0:
+        return False
     # judge on [[4,2,2]]
     H4 = np.ones((1, 4), np.uint8)
     z = np.zeros(4, np.uint8)
@@ -79,6 +102,15 @@ MUTATIONS = {
     "FWS ties to last": ("mbbp_oracle.c", "cnt * (best_w + 1) > best_cnt * (w + 1)",
                          "cnt * (best_w + 1) >= best_cnt * (w + 1)"),
     "judge rank test inverted": ("mbbp_oracle.c", "> base ? 2 : 0", ">= base ? 2 : 0"),
+    "serial: stale check messages": ("bp_body.inc", "                        q = q + c2v[k];\n", ""),
+    "serial: own edge not excluded": ("bp_body.inc", "if (k == j) continue;\n                        q = q + c2v[k];",
+                                      "q = q + c2v[k];"),
+    "serial: syndrome sign dropped": ("bp_body.inc", "int neg = st[r] & 1;\n                    if (rule == OR_RULE_NMS) {",
+                                      "int neg = 0;\n                    if (rule == OR_RULE_NMS) {"),
+    "serial: layers ignore shared variables": ("bp_body.inc", "if (used[(size_t)L * (n + 1) + edge_col[k]]) clash = 1;",
+                                               "if (used[(size_t)L * (n + 1) + edge_col[k]]) clash = 0;"),
+    "LMS ties to last": ("mbbp_oracle.c", "mt < best_m", "mt <= best_m"),
+    "LMS metric drops the sign of mu": ("mbbp_oracle.c", "mt = mt + mu[v];", "mt = mt + fabsf(mu[v]);"),
 }
 
 
