@@ -124,12 +124,32 @@ mbbp_status mbbp_build_bases_from_sets(const uint8_t* H, int m, int n, int R,
                                        const int32_t* set_ptr, const int32_t* set_rows,
                                        mbbp_bases** out);
 
+/* Random augmentation, the comparison of Table II: representation t gets
+ * sizes[t] distinct rows of H (at most m), the first entries of the
+ * Fisher-Yates shuffle of 0..m-1 that mbbp_permutation(seed, t + 1, m)
+ * defines.  sizes: host int32[R]; set_ptr: host int32[R+1]; set_rows: host
+ * int32[sum of min(sizes[t], m)].  Pass the result to
+ * mbbp_build_bases_from_sets (e.g. with the sizes of the subtrees it
+ * replaces, which keeps the number of duplicated rows). */
+mbbp_status mbbp_random_sets(int m, int R, const int32_t* sizes, uint64_t seed,
+                             int32_t* set_ptr, int32_t* set_rows);
+
 /* Shape of a handle.  Each output is host memory or NULL: m, n, R (int32);
  * rows, edges (int32[R]: rows and edges of each H^(t)); set_ptr (int32[R+1])
  * and set_rows (int32[set_ptr[R]]): the extra rows. */
 mbbp_status mbbp_bases_info(const mbbp_bases* B, int32_t* m, int32_t* n, int32_t* R,
                             int32_t* rows, int32_t* edges, int32_t* set_ptr,
                             int32_t* set_rows);
+
+/* Check order of the serial schedule of representation t (see
+ * mbbp_decode_ex): the rows of H^(t) split greedily, in row order, into
+ * layers of rows that share no variable (each row joins the first layer it
+ * does not clash with).  order: host int32[rows of H^(t)] or NULL, the rows
+ * layer by layer (ascending inside a layer); layer_ptr: host
+ * int32[rows + 1] or NULL, layer L holds order[layer_ptr[L] ..
+ * layer_ptr[L+1]); n_layers: host int32 or NULL. */
+mbbp_status mbbp_bases_layers(const mbbp_bases* B, int t, int32_t* order, int32_t* layer_ptr,
+                              int32_t* n_layers);
 
 /* Free a handle and its device tables (NULL is a no-op).  Not stream-ordered:
  * no work that uses B may still be pending. */
@@ -194,6 +214,45 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
                         uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run,
                         uint8_t* success, int16_t* selected, float* posterior,
                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* Decoder options: the BP schedule and the decision rule. */
+#define MBBP_SCHEDULE_FLOODING 0
+#define MBBP_SCHEDULE_SERIAL 1
+#define MBBP_DECISION_FWS 0
+#define MBBP_DECISION_LMS 1
+
+typedef struct {
+    int rule;      /* MBBP_RULE_NMS or MBBP_RULE_SP                        */
+    float alpha;   /* normalization of Eq. (2), 0 < alpha <= 1 (NMS only)   */
+    int schedule;  /* MBBP_SCHEDULE_*                                      */
+    int decision;  /* MBBP_DECISION_*                                      */
+} mbbp_options;
+
+/* mbbp_decode with a choice of schedule and decision rule; every argument
+ * other than opt (host pointer, not kept) is that of mbbp_decode, and
+ * {rule, alpha, FLOODING, FWS} gives mbbp_decode's result.
+ *
+ * MBBP_SCHEDULE_SERIAL (Section II-B: checks are updated one after the other
+ * and the newest messages are used within the iteration; the numerical
+ * results run MBBP-LD this way): check messages start at 0; an iteration
+ * visits the checks of H^(t) in the layer order of mbbp_bases_layers, and a
+ * visited check first forms q_{v->c} = mu_v + the current messages of v's
+ * other checks (ascending row order, clamped to +-MBBP_LMAX), then replaces
+ * its messages by the check rule.  After the last layer come the
+ * posteriors, hard decisions and the halting test of mbbp_decode.  Rows of a
+ * layer share no variable, so the kernel updates a layer's rows at once and
+ * the result equals the one-check-at-a-time order.
+ *
+ * MBBP_DECISION_LMS (the least-metric selector of classical MBBP, Section
+ * III-A): among the converged candidates, the one with the smallest
+ * sum_i mu_i e_i, with mu the shot's LLRs and the sum a float sum in
+ * ascending i; ties go to the lowest representation index; none converged
+ * -> e_hat = 0, selected = -1. */
+mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                           const float* llr, int llr_stride, int iters, const mbbp_options* opt,
+                           uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run,
+                           uint8_t* success, int16_t* selected, float* posterior,
+                           void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * Mixed batches: several codes decoded by one persistent launch.

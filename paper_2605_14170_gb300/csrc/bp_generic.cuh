@@ -51,13 +51,11 @@ __device__ __forceinline__ float phi(float x) {
 }
 
 // Check-node update of row r (Eq. (2) with the syndrome sign, or the
-// sum-product rule).  deg <= DC edges at slots j * MP + r.
+// sum-product rule) from its incoming messages q[0..deg) (q[j] = MBBP_LMAX
+// for j >= deg); writes the deg outgoing messages to slots j * MP + r.
 template <int DC, int RULE>
-__device__ __forceinline__ void check_row(float* msg, int r, int MP, int deg, uint32_t sbit,
-                                          float alpha) {
-    float q[DC];
-#pragma unroll
-    for (int j = 0; j < DC; ++j) q[j] = (j < deg) ? msg[j * MP + r] : MBBP_LMAX;
+__device__ __forceinline__ void check_out(const float (&q)[DC], float* msg, int r, int MP, int deg,
+                                          uint32_t sbit, float alpha) {
     if (RULE == MBBP_RULE_NMS) {
         float min1 = MBBP_LMAX, min2 = MBBP_LMAX;
         uint32_t par = sbit;
@@ -104,6 +102,16 @@ __device__ __forceinline__ void check_row(float* msg, int r, int MP, int deg, ui
     }
 }
 
+// Flooding check pass of row r: its q messages are in its own slots.
+template <int DC, int RULE>
+__device__ __forceinline__ void check_row(float* msg, int r, int MP, int deg, uint32_t sbit,
+                                          float alpha) {
+    float q[DC];
+#pragma unroll
+    for (int j = 0; j < DC; ++j) q[j] = (j < deg) ? msg[j * MP + r] : MBBP_LMAX;
+    check_out<DC, RULE>(q, msg, r, MP, deg, sbit, alpha);
+}
+
 // Variable-node update of a degree-D variable (Eq. (3)): q_i = mu + sum of
 // the other messages in ascending row order, clamped; returns the posterior.
 template <int D>
@@ -139,6 +147,28 @@ __device__ __forceinline__ float var_dispatch(int deg, float* msg, const uint16_
     }
 }
 
+
+// Bit-pack the hard decision eh[0..n) into the candidate words of `item`,
+// and store the convergence flag and iteration count.
+__device__ __forceinline__ void store_item(const ShotIO& io, unsigned long long item, int n, int W,
+                                           const uint8_t* eh, bool conv, int K) {
+    const int lane = threadIdx.x & 31;
+    uint32_t myword = 0;
+    for (int w = 0; w < W; ++w) {
+        const int v = 32 * w + lane;
+        const uint32_t bit = (v < n) ? (uint32_t)eh[v] : 0u;
+        const uint32_t word = __ballot_sync(kFull, bit);
+        if ((w & 31) == lane) myword = word;
+        if ((w & 31) == 31 || w == W - 1) {
+            const int base = w & ~31;
+            if (base + lane <= w) io.cand[item * W + base + lane] = myword;
+        }
+    }
+    if (lane == 0) {
+        io.conv[item] = conv ? 1 : 0;
+        if (io.iters_run) io.iters_run[item] = (uint16_t)K;
+    }
+}
 
 // Decode one (shot, representation) item.  area: this warp's shared-memory
 // area (warp_layout(DC, ...).per_warp bytes); hcol: columns of the rows of H
@@ -228,21 +258,127 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
         __syncwarp();
     }
     // candidate e_t (bit-packed), convergence flag, iterations
-    uint32_t myword = 0;
-    for (int w = 0; w < W; ++w) {
-        const int v = 32 * w + lane;
-        const uint32_t bit = (v < n) ? (uint32_t)eh[v] : 0u;
+    store_item(io, item, n, W, eh, conv, K);
+    __syncwarp();
+}
+
+// Per-warp shared memory of the serial schedule: the flooding layout plus
+// the syndrome bits of the rows of H^(t) (MP / 32 words).
+__host__ __device__ __forceinline__ int serial_warp_bytes(int DC, int MP, int mpad, int n) {
+    return warp_layout(DC, MP, mpad, n).per_warp + align16(MP / 8);
+}
+
+// Decode one (shot, representation) item with the serial schedule.  The
+// edge slots hold m_{c->v} for the whole decode.  Within a layer the rows
+// share no variable: lane-parallel rows read only messages of other layers'
+// rows (through their variables) and write only their own slots, so the
+// layer's result is that of visiting its rows one by one.  q_{v->c} is
+// mu_v plus v's other messages in ascending row order (the slot list of v
+// is sorted that way), clamped, exactly as the oracle forms it.
+template <int DC, int DV, int RULE>
+__device__ __forceinline__ void run_item_serial(const DevBases& B, const ShotIO& io, int shot, int b,
+                                                unsigned char* area, const uint16_t* hcol) {
+    const int lane = threadIdx.x & 31;
+    const int MP = B.MP, n = B.n, m = B.m, R = B.R, W = B.W, mpad = B.mpad;
+    const WarpLayout L = warp_layout(DC, MP, mpad, n);
+    float* msg = reinterpret_cast<float*>(area);
+    float* mu_s = msg + L.S;
+    uint8_t* eh = reinterpret_cast<uint8_t*>(mu_s + L.npad);
+    uint32_t* sbits = reinterpret_cast<uint32_t*>(area + L.per_warp);
+    const int row_steps = MP >> 5;
+    const int orow_steps = mpad >> 5;
+    const unsigned long long item = (unsigned long long)shot * R + b;
+    const uint32_t* rinfo = B.rowinfo + (size_t)b * MP;
+    const uint2* vd = B.vdesc + (size_t)b * n;
+    const uint16_t* lrows = B.lrows + (size_t)b * MP;
+    const uint16_t* lptr = B.lptr + (size_t)b * (MP + 1);
+    const uint2* ev = B.evar + (size_t)b * DC * MP;
+    const int nl = __ldg(B.nlayers + b);
+    const int Mb = __ldg(B.rows + b);
+    const float* llr = io.llr + (size_t)shot * io.llr_stride;
+    const uint8_t* sy = io.synd + (size_t)shot * m;
+
+    __syncwarp();
+    for (int v = lane; v < n; v += 32) {
+        const float x = __ldg(llr + v);
+        mu_s[v] = x;
+        eh[v] = (x < 0.f) ? 1 : 0;
+        if (io.post) io.post[item * n + v] = x;
+    }
+    if (lane == 0) eh[n] = 0;
+    for (int i = lane; i < L.S; i += 32) msg[i] = 0.0f;  // m^(0)_{c->v} = 0
+    uint32_t sb = 0;  // syndrome bits of the rows lane + 32k (halting test)
+    for (int k = 0; k < row_steps; ++k) {
+        const int r = lane + 32 * k;
+        const uint32_t bit = (r < Mb) ? (uint32_t)(__ldg(sy + (__ldg(rinfo + r) & 0xffffu)) & 1u) : 0u;
+        sb |= bit << k;
         const uint32_t word = __ballot_sync(kFull, bit);
-        if ((w & 31) == lane) myword = word;
-        if ((w & 31) == 31 || w == W - 1) {
-            const int base = w & ~31;
-            if (base + lane <= w) io.cand[item * W + base + lane] = myword;
+        if (lane == 0) sbits[k] = word;
+    }
+    __syncwarp();
+
+    int K = 0;
+    bool conv = false;
+    for (int it = 0;; ++it) {
+        bool ok = true;
+        for (int k = 0; k < orow_steps; ++k) {
+            const int r = lane + 32 * k;
+            if (r < m) {
+                uint32_t par = (sb >> k) & 1u;
+#pragma unroll
+                for (int j = 0; j < DC; ++j) par ^= eh[hcol[j * mpad + r]];
+                ok = ok && (par == 0u);
+            }
         }
+        if (__all_sync(kFull, ok)) {
+            conv = true;
+            K = it;
+            break;
+        }
+        if (it == io.iters) {
+            K = it;
+            break;
+        }
+        for (int l = 0; l < nl; ++l) {
+            const int i1 = __ldg(lptr + l + 1);
+            for (int idx = __ldg(lptr + l) + lane; idx < i1; idx += 32) {
+                const int r = __ldg(lrows + idx);
+                const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
+                float q[DC];
+#pragma unroll
+                for (int j = 0; j < DC; ++j) {
+                    q[j] = MBBP_LMAX;
+                    if (j < deg) {
+                        const int slot = j * MP + r;
+                        const uint2 e = __ldg(ev + slot);
+                        const int dv = (int)(e.y >> 16);
+                        float x = mu_s[e.y & 0xffffu];
+#pragma unroll
+                        for (int i = 0; i < DV; ++i) {
+                            if (i < dv) {
+                                const int sl = __ldg(B.vslot + e.x + i);
+                                if (sl != slot) x = __fadd_rn(x, msg[sl]);
+                            }
+                        }
+                        q[j] = fminf(fmaxf(x, -MBBP_LMAX), MBBP_LMAX);
+                    }
+                }
+                check_out<DC, RULE>(q, msg, r, MP, deg, (sbits[r >> 5] >> (r & 31)) & 1u, io.alpha);
+            }
+            __syncwarp();
+        }
+        // posterior mu_v + all messages of v (ascending row), hard decision
+        for (int p = lane; p < n; p += 32) {
+            const uint2 d = __ldg(vd + p);
+            const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
+            float P = mu_s[v];
+            for (int i = 0; i < deg; ++i) P = __fadd_rn(P, msg[__ldg(B.vslot + d.x + i)]);
+            eh[v] = (P < 0.f) ? 1 : 0;
+            if (io.post) io.post[item * n + v] = P;
+        }
+        __syncwarp();
     }
-    if (lane == 0) {
-        io.conv[item] = conv ? 1 : 0;
-        if (io.iters_run) io.iters_run[item] = (uint16_t)K;
-    }
+    store_item(io, item, n, W, eh, conv, K);
     __syncwarp();
 }
 

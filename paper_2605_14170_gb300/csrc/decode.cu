@@ -47,6 +47,33 @@ decode_kernel(const DecodeArgs a) {
     }
 }
 
+// The serial-schedule kernel: same work list as decode_kernel, one warp per
+// (shot, representation) item, run_item_serial per item.
+template <int DC, int DV, int RULE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+decode_serial_kernel(const DecodeArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevBases& B = a.B;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int R = B.R;
+    const generic_bp::WarpLayout L = generic_bp::warp_layout(DC, B.MP, B.mpad, B.n);
+    const int per_warp = generic_bp::serial_warp_bytes(DC, B.MP, B.mpad, B.n);
+    uint16_t* hcol_s = reinterpret_cast<uint16_t*>(smem);
+    unsigned char* area = smem + L.hcol_bytes + warp * per_warp;
+    for (int i = threadIdx.x; i < DC * B.mpad; i += blockDim.x) hcol_s[i] = __ldg(B.hcol + i);
+    __syncthreads();
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= a.total_items) break;
+        const int shot = (int)(item / (unsigned long long)R);
+        const int b = (int)(item - (unsigned long long)shot * R);
+        generic_bp::run_item_serial<DC, DV, RULE>(B, a.io, shot, b, area, hcol_s);
+    }
+}
+
 struct FwsBest {
     long long cnt, w;
     int idx, valid;
@@ -111,6 +138,76 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fws_kernel(const FwsArgs 
         a.success[shot] = sel >= 0 ? 1 : 0;
         if (a.selected) a.selected[shot] = (int16_t)sel;
     }
+}
+
+// One warp per shot: the least-metric selector over the R candidates
+// (R <= 64).  The metric of candidate a is the float sum, in ascending
+// variable order, of the shot's LLRs over the set bits of a; the smallest
+// metric wins, ties to the lowest index.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) lms_kernel(const FwsArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int shot = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (shot >= a.batch) return;  // uniform per warp
+    const int R = a.R, W = a.W, n = a.n;
+    const uint32_t* src = a.cand + (size_t)shot * R * W;
+    const uint8_t* cv = a.conv + (size_t)shot * R;
+    const float* mu = a.llr + (size_t)shot * a.llr_stride;
+    float best_m = 0.0f;
+    int best = -1;  // lowest index among this lane's minima
+    for (int h = 0; h < 2; ++h) {
+        const int ai = lane + 32 * h;
+        if (ai < R && __ldg(cv + ai)) {
+            const uint32_t* ca = src + (size_t)ai * W;
+            float mt = 0.0f;
+            for (int k = 0; k < W; ++k) {
+                uint32_t word = __ldg(ca + k);
+                while (word) {
+                    const int bit = __ffs(word) - 1;
+                    mt = __fadd_rn(mt, __ldg(mu + 32 * k + bit));
+                    word &= word - 1u;
+                }
+            }
+            if (best < 0 || mt < best_m) {
+                best = ai;
+                best_m = mt;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float om = __shfl_xor_sync(kFull, best_m, off);
+        const int ob = __shfl_xor_sync(kFull, best, off);
+        if (ob >= 0 && (best < 0 || om < best_m || (om == best_m && ob < best))) {
+            best = ob;
+            best_m = om;
+        }
+    }
+    uint8_t* out = a.e_hat + (size_t)shot * n;
+    for (int v = lane; v < n; v += 32)
+        out[v] = (best >= 0) ? (uint8_t)((__ldg(src + (size_t)best * W + (v >> 5)) >> (v & 31)) & 1u) : 0;
+    if (lane == 0) {
+        a.success[shot] = best >= 0 ? 1 : 0;
+        if (a.selected) a.selected[shot] = (int16_t)best;
+    }
+}
+
+template <int K, int RULE>
+cudaError_t launch_serial_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
+    auto kern = decode_serial_kernel<K, K, RULE>;
+    const generic_bp::WarpLayout L = generic_bp::warp_layout(K, a.B.MP, a.B.mpad, a.B.n);
+    const int per_warp = generic_bp::serial_warp_bytes(K, a.B.MP, a.B.mpad, a.B.n);
+    int warps = kWarpsPerBlock;
+    while (warps > 1 && (size_t)L.hcol_bytes + (size_t)warps * per_warp > 200 * 1024) --warps;
+    const size_t smem = (size_t)L.hcol_bytes + (size_t)warps * per_warp;
+    int per_sm = 0;
+    cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kern), warps * 32, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    unsigned long long want = (a.total_items + warps - 1) / warps;
+    unsigned long long grid = (unsigned long long)per_sm * (unsigned long long)sm_count;
+    if (want < grid) grid = want;
+    kern<<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int K, int RULE>
@@ -205,7 +302,28 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count) {
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_decode_serial(const DecodeArgs& a, cudaStream_t s, int sm_count) {
+    const int K = a.B.DC;
+    if (a.rule == MBBP_RULE_NMS) {
+        if (K == 6) return launch_serial_t<6, MBBP_RULE_NMS>(a, s, sm_count);
+        if (K == 8) return launch_serial_t<8, MBBP_RULE_NMS>(a, s, sm_count);
+        if (K == 12) return launch_serial_t<12, MBBP_RULE_NMS>(a, s, sm_count);
+    } else {
+        if (K == 6) return launch_serial_t<6, MBBP_RULE_SP>(a, s, sm_count);
+        if (K == 8) return launch_serial_t<8, MBBP_RULE_SP>(a, s, sm_count);
+        if (K == 12) return launch_serial_t<12, MBBP_RULE_SP>(a, s, sm_count);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_fws(const FwsArgs& a, cudaStream_t s) {
+    if (a.decision == MBBP_DECISION_LMS) {
+        if (!a.llr) return cudaErrorInvalidValue;
+        const int warps = kWarpsPerBlock;
+        const unsigned grid = (unsigned)((a.batch + warps - 1) / warps);
+        lms_kernel<<<grid, warps * 32, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     const size_t per_warp = (size_t)a.R * a.W * 4;
     int warps = kWarpsPerBlock;
     while (warps > 1 && warps * per_warp > 96 * 1024) --warps;

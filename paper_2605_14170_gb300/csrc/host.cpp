@@ -20,6 +20,7 @@ struct mbbp_bases {
     int device = 0, sm_count = 0;
     std::vector<uint8_t> H;
     std::vector<int32_t> set_ptr, set_rows, rows, edges;
+    std::vector<int32_t> lorder, lptr, nlayers;  // serial schedule, [R][MP], [R][MP+1], [R]
     void* dmem = nullptr;
     DevBases dev{};
 };
@@ -352,6 +353,10 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     std::vector<uint2> vdesc((size_t)R * n);
     std::vector<uint16_t> vslot;
     std::vector<int32_t> rows(R), edges(R);
+    std::vector<uint2> evar((size_t)R * K * MP, make_uint2(0, 0));
+    B->lorder.assign((size_t)R * MP, 0);
+    B->lptr.assign((size_t)R * (MP + 1), 0);
+    B->nlayers.assign(R, 0);
     for (int t = 0; t < R; ++t) {
         const int extra = set_ptr[t + 1] - set_ptr[t];
         const int M = m + extra;
@@ -371,15 +376,49 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         for (int v = 0; v < n; ++v) ord[v] = v;
         std::stable_sort(ord.begin(), ord.end(),
                          [&](int a, int b) { return vl[a].size() < vl[b].size(); });
+        std::vector<uint2> vstart(n);
         for (int p = 0; p < n; ++p) {
             const int v = ord[p];
             uint2 d;
             d.x = (uint32_t)vslot.size();
             d.y = (uint32_t)v | ((uint32_t)vl[v].size() << 16);
             vdesc[(size_t)t * n + p] = d;
+            vstart[v] = d;
             vslot.insert(vslot.end(), vl[v].begin(), vl[v].end());
         }
+        // Serial schedule: every edge slot points at its variable's slot list;
+        // rows go, in row order, into the first layer holding none of their
+        // variables.
+        std::vector<std::vector<uint8_t>> layer_vars;
+        std::vector<int> layer_of(M);
+        for (int r = 0; r < M; ++r) {
+            const int src = r < m ? r : set_rows[set_ptr[t] + (r - m)];
+            const auto& cols = g.rcols[src];
+            for (int j = 0; j < (int)cols.size(); ++j) evar[(size_t)t * K * MP + (size_t)j * MP + r] = vstart[cols[j]];
+            size_t L = 0;
+            for (; L < layer_vars.size(); ++L) {
+                bool clash = false;
+                for (int v : cols) clash = clash || layer_vars[L][v];
+                if (!clash) break;
+            }
+            if (L == layer_vars.size()) layer_vars.emplace_back(n, 0);
+            for (int v : cols) layer_vars[L][v] = 1;
+            layer_of[r] = (int)L;
+        }
+        const int nl = (int)layer_vars.size();
+        int32_t* lo = B->lorder.data() + (size_t)t * MP;
+        int32_t* lp = B->lptr.data() + (size_t)t * (MP + 1);
+        int pos = 0;
+        for (int L = 0; L < nl; ++L) {
+            lp[L] = pos;
+            for (int r = 0; r < M; ++r)
+                if (layer_of[r] == L) lo[pos++] = r;
+        }
+        lp[nl] = pos;
+        B->nlayers[t] = nl;
     }
+    std::vector<uint16_t> lrows16(B->lorder.begin(), B->lorder.end());
+    std::vector<uint16_t> lptr16(B->lptr.begin(), B->lptr.end());
     // Small-code tables (register-resident kernel), when a shape fits.
     int shape = 0;
     if (K == 6)
@@ -460,7 +499,11 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     const size_t o_vdesc2 = o_rowptr + align256(rowptr.size() * 4);
     const size_t o_rinfo2 = o_vdesc2 + align256(vdesc2.size() * sizeof(uint4));
     const size_t o_hmask2 = o_rinfo2 + align256(rinfo2.size() * 4);
-    const size_t total = o_hmask2 + align256(hmask2.size() * 4);
+    const size_t o_lrows = o_hmask2 + align256(hmask2.size() * 4);
+    const size_t o_lptr = o_lrows + align256(lrows16.size() * 2);
+    const size_t o_nlayers = o_lptr + align256(lptr16.size() * 2);
+    const size_t o_evar = o_nlayers + align256((size_t)R * 4);
+    const size_t total = o_evar + align256(evar.size() * sizeof(uint2));
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
     if (e == cudaSuccess) e = cudaMalloc(&B->dmem, total);
@@ -480,6 +523,10 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         {o_vdesc2, vdesc2.data(), vdesc2.size() * sizeof(uint4)},
         {o_rinfo2, rinfo2.data(), rinfo2.size() * 4},
         {o_hmask2, hmask2.data(), hmask2.size() * 4},
+        {o_lrows, lrows16.data(), lrows16.size() * 2},
+        {o_lptr, lptr16.data(), lptr16.size() * 2},
+        {o_nlayers, B->nlayers.data(), (size_t)R * 4},
+        {o_evar, evar.data(), evar.size() * sizeof(uint2)},
     };
     for (const Copy& c : copies) {
         if (c.bytes == 0) continue;
@@ -507,6 +554,10 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     d.vdesc2 = shape ? reinterpret_cast<const uint4*>(base + o_vdesc2) : nullptr;
     d.rinfo2 = shape ? reinterpret_cast<const uint32_t*>(base + o_rinfo2) : nullptr;
     d.hmask2 = shape ? reinterpret_cast<const uint32_t*>(base + o_hmask2) : nullptr;
+    d.lrows = reinterpret_cast<const uint16_t*>(base + o_lrows);
+    d.lptr = reinterpret_cast<const uint16_t*>(base + o_lptr);
+    d.nlayers = reinterpret_cast<const int32_t*>(base + o_nlayers);
+    d.evar = reinterpret_cast<const uint2*>(base + o_evar);
     *out = B;
     return MBBP_OK;
 }
@@ -627,6 +678,39 @@ mbbp_status mbbp_bases_info(const mbbp_bases* B, int32_t* m, int32_t* n, int32_t
     return MBBP_OK;
 }
 
+mbbp_status mbbp_bases_layers(const mbbp_bases* B, int t, int32_t* order, int32_t* layer_ptr,
+                              int32_t* n_layers) {
+    if (!B) return fail(MBBP_E_INVALID, "mbbp_bases_layers: NULL handle");
+    if (t < 0 || t >= B->R) return fail(MBBP_E_INVALID, "mbbp_bases_layers: t out of range");
+    const int M = B->rows[t], nl = B->nlayers[t];
+    if (order) std::copy_n(B->lorder.begin() + (size_t)t * B->MP, M, order);
+    if (layer_ptr) std::copy_n(B->lptr.begin() + (size_t)t * (B->MP + 1), nl + 1, layer_ptr);
+    if (n_layers) *n_layers = nl;
+    return MBBP_OK;
+}
+
+mbbp_status mbbp_random_sets(int m, int R, const int32_t* sizes, uint64_t seed, int32_t* set_ptr,
+                             int32_t* set_rows) {
+    if (m < 1 || R < 0) return fail(MBBP_E_INVALID, "mbbp_random_sets: bad sizes");
+    if (R > 0 && (!sizes || !set_ptr)) return fail(MBBP_E_INVALID, "mbbp_random_sets: NULL buffer");
+    if (R == 0) {
+        if (set_ptr) set_ptr[0] = 0;
+        return MBBP_OK;
+    }
+    for (int t = 0; t < R; ++t)
+        if (sizes[t] < 0) return fail(MBBP_E_INVALID, "mbbp_random_sets: negative size");
+    std::vector<int32_t> perm(m);
+    set_ptr[0] = 0;
+    for (int t = 0; t < R; ++t) {
+        permutation_impl(seed, t + 1, m, perm.data());
+        const int k = std::min(sizes[t], m);
+        if (k > 0 && !set_rows) return fail(MBBP_E_INVALID, "mbbp_random_sets: set_rows is NULL");
+        std::copy_n(perm.begin(), k, set_rows + set_ptr[t]);
+        set_ptr[t + 1] = set_ptr[t] + k;
+    }
+    return MBBP_OK;
+}
+
 void mbbp_bases_free(mbbp_bases* B) {
     if (!B) return;
     if (B->dmem) cudaFree(B->dmem);
@@ -666,7 +750,28 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
                         uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,
                         int16_t* selected, float* posterior, void* workspace,
                         size_t workspace_bytes, void* stream) {
+    mbbp_options o{};
+    o.rule = rule;
+    o.alpha = alpha;
+    o.schedule = MBBP_SCHEDULE_FLOODING;
+    o.decision = MBBP_DECISION_FWS;
+    return mbbp_decode_ex(B, batch, syndromes, llr, llr_stride, iters, &o, e_hat, conv, iters_run,
+                          success, selected, posterior, workspace, workspace_bytes, stream);
+}
+
+mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                           const float* llr, int llr_stride, int iters, const mbbp_options* opt,
+                           uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,
+                           int16_t* selected, float* posterior, void* workspace,
+                           size_t workspace_bytes, void* stream) {
     if (!B) return fail(MBBP_E_INVALID, "mbbp_decode: NULL handle");
+    if (!opt) return fail(MBBP_E_INVALID, "mbbp_decode_ex: NULL options");
+    const int rule = opt->rule;
+    const float alpha = opt->alpha;
+    if (opt->schedule != MBBP_SCHEDULE_FLOODING && opt->schedule != MBBP_SCHEDULE_SERIAL)
+        return fail(MBBP_E_INVALID, "unknown schedule");
+    if (opt->decision != MBBP_DECISION_FWS && opt->decision != MBBP_DECISION_LMS)
+        return fail(MBBP_E_INVALID, "unknown decision rule");
     if (batch < 0) return fail(MBBP_E_INVALID, "batch must be >= 0");
     if (iters < 0 || iters > MBBP_MAX_ITERS) return fail(MBBP_E_INVALID, "iters out of range");
     if (rule != MBBP_RULE_NMS && rule != MBBP_RULE_SP) return fail(MBBP_E_INVALID, "unknown rule");
@@ -699,7 +804,9 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
     a.io.post = posterior;
     a.total_items = (unsigned long long)batch * B->R;
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = launch_decode(a, s, B->sm_count);
+    if (e == cudaSuccess)
+        e = opt->schedule == MBBP_SCHEDULE_SERIAL ? launch_decode_serial(a, s, B->sm_count)
+                                                  : launch_decode(a, s, B->sm_count);
     if (e != cudaSuccess) return cuda_fail(e, "mbbp_decode (BP)");
     FwsArgs f{};
     f.cand = a.io.cand;
@@ -711,8 +818,11 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
     f.e_hat = e_hat;
     f.success = success;
     f.selected = selected;
+    f.decision = opt->decision;
+    f.llr = llr;
+    f.llr_stride = llr_stride;
     e = launch_fws(f, s);
-    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_decode (FWS)");
+    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_decode (selection)");
 }
 
 mbbp_status mbbp_decode_noalloc(const mbbp_bases* B, int batch, const uint8_t* syndromes,

@@ -41,6 +41,14 @@ struct DevBases {
     const uint32_t* rinfo2;   // [R][MP] ELL index -> src row | degree << 16
     const uint32_t* hmask2;   // [R][VS][ORS*32] rows of H as bit masks over positions
     int shape, VS, RS, ORS;
+
+    // Serial schedule: rows of H^(t) in layer order, layer boundaries and,
+    // per edge slot, the variable's slot list (x = first vslot entry,
+    // y = variable | degree << 16).
+    const uint16_t* lrows;    // [R][MP]
+    const uint16_t* lptr;     // [R][MP+1]
+    const int32_t* nlayers;   // [R]
+    const uint2* evar;        // [R][DC*MP]
 };
 
 // Bank rotation of edge position j in the small-code layout.
@@ -80,6 +88,9 @@ struct FwsArgs {
     uint8_t* e_hat;
     uint8_t* success;
     int16_t* selected;
+    int decision;             // MBBP_DECISION_FWS or MBBP_DECISION_LMS
+    const float* llr;         // LMS metric weights: [n] or [batch][llr_stride]
+    int llr_stride;
 };
 
 struct DevLogicals {
@@ -142,6 +153,7 @@ cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, size_t c
 
 // Launchers (decode.cu, decode_small.cu, aux.cu).  They return cudaGetLastError().
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_decode_serial(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_decode_small(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_fws(const FwsArgs& a, cudaStream_t s);
 size_t decode_smem_bytes(const DevBases& B, int warps);

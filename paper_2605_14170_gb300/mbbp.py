@@ -22,6 +22,10 @@ LIB_PATH = os.path.join(_HERE, "libmbbp.so")
 
 RULE_NMS = 0
 RULE_SP = 1
+SCHEDULE_FLOODING = 0
+SCHEDULE_SERIAL = 1
+DECISION_FWS = 0
+DECISION_LMS = 1
 NOISE_BSC = 0
 NOISE_DEPOLARIZING = 1
 MAX_R = 64
@@ -49,6 +53,11 @@ class CodeIO(C.Structure):
                 ("iters_run", C.c_void_p), ("success", C.c_void_p), ("selected", C.c_void_p)]
 
 
+class Options(C.Structure):
+    """mbbp_options: check rule, alpha, schedule and decision rule."""
+    _fields_ = [("rule", C.c_int), ("alpha", C.c_float), ("schedule", C.c_int), ("decision", C.c_int)]
+
+
 _i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
 _u8p = np.ctypeslib.ndpointer(np.uint8, flags="C")
 _vp = C.c_void_p
@@ -61,7 +70,9 @@ _sig = {
     "mbbp_build_bases": (C.c_int, [_u8p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_vp)]),
     "mbbp_build_bases_from_sets": (C.c_int, [_u8p, C.c_int, C.c_int, C.c_int, _i32p, _i32p,
                                              C.POINTER(_vp)]),
+    "mbbp_random_sets": (C.c_int, [C.c_int, C.c_int, _i32p, C.c_uint64, _i32p, _i32p]),
     "mbbp_bases_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mbbp_bases_layers": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "mbbp_bases_free": (None, [_vp]),
     "mbbp_sample_errors": (C.c_int, [C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
                                      _vp, _vp, _vp]),
@@ -69,6 +80,8 @@ _sig = {
     "mbbp_decode_workspace_size": (C.c_size_t, [_vp, C.c_int]),
     "mbbp_decode": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
                               _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "mbbp_decode_ex": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.POINTER(Options),
+                                 _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_decode_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
                                       _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mbbp_plan_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
@@ -230,6 +243,27 @@ def mbbp_bases_info(B: Bases) -> dict:
     return {"m": m.value, "n": n.value, "R": R_, "rows": rows, "edges": edges, "sets": sets}
 
 
+def mbbp_random_sets(m: int, sizes, seed: int) -> list:
+    """Random augmentation sets (Table II): list of int32 row arrays."""
+    sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+    R = len(sizes)
+    ptr = np.zeros(R + 1, np.int32)
+    rows = np.zeros(max(int(np.minimum(sizes, m).sum()), 1), np.int32)
+    _check(_lib.mbbp_random_sets(m, R, sizes, seed, ptr, rows), "mbbp_random_sets")
+    return [rows[ptr[t]:ptr[t + 1]].copy() for t in range(R)]
+
+
+def mbbp_bases_layers(B: Bases, t: int) -> list:
+    """Layers of the serial schedule of representation t: list of row arrays."""
+    nl = C.c_int32()
+    _check(_lib.mbbp_bases_layers(B.handle, t, None, None, C.cast(C.pointer(nl), _vp)), "mbbp_bases_layers")
+    info = mbbp_bases_info(B)
+    order = np.zeros(int(info["rows"][t]), np.int32)
+    ptr = np.zeros(nl.value + 1, np.int32)
+    _check(_lib.mbbp_bases_layers(B.handle, t, _np_ptr(order), _np_ptr(ptr), None), "mbbp_bases_layers")
+    return [order[ptr[L]:ptr[L + 1]].copy() for L in range(nl.value)]
+
+
 # ----------------------------------------------------------------- device
 
 def mbbp_sample_errors(n: int, batch: int, first_shot: int, seed: int, p: float, noise: int,
@@ -269,6 +303,23 @@ def mbbp_decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int, e
         _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
         _dptr(posterior, torch.float32, "posterior"), _dptr(workspace, torch.uint8, "workspace"),
         workspace.numel(), _stream(stream)), "mbbp_decode")
+
+
+def mbbp_decode_ex(B: Bases, syndromes, llr, iters: int, opt: Options, e_hat, conv, success, workspace,
+                   iters_run=None, selected=None, posterior=None, stream=None) -> None:
+    """mbbp_decode with a schedule and a decision rule (Options)."""
+    import torch
+    batch = syndromes.shape[0]
+    if syndromes.numel() != batch * B.m:
+        raise ValueError("syndromes must be [batch, m]")
+    stride = 0 if llr.dim() == 1 else llr.shape[-1]
+    _check(_lib.mbbp_decode_ex(
+        B.handle, batch, _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
+        stride, iters, C.byref(opt), _dptr(e_hat, torch.uint8, "e_hat"),
+        _dptr(conv, torch.uint8, "conv"), _dptr(iters_run, torch.int16, "iters_run"),
+        _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
+        _dptr(posterior, torch.float32, "posterior"), _dptr(workspace, torch.uint8, "workspace"),
+        workspace.numel(), _stream(stream)), "mbbp_decode_ex")
 
 
 def mbbp_decode_noalloc(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int, e_hat, conv,
@@ -539,8 +590,10 @@ def mbbp_judge(L: Logicals, e, e_hat, fail=None, counts=None, stream=None) -> No
 # ----------------------------------------------------------------- helpers
 
 def decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int = RULE_NMS,
-           want_posterior: bool = False, stream=None) -> dict:
-    """Allocate the outputs with torch and call ``mbbp_decode``.
+           want_posterior: bool = False, stream=None, schedule: int = SCHEDULE_FLOODING,
+           decision: int = DECISION_FWS) -> dict:
+    """Allocate the outputs with torch and call ``mbbp_decode`` (or
+    ``mbbp_decode_ex`` for the serial schedule or the LMS decision).
 
     Returns a dict of CUDA tensors: e_hat [batch, n], conv [batch, R],
     iters [batch, R] (int16 holding uint16), success [batch], selected
@@ -560,8 +613,13 @@ def decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int = RULE_
     ws = torch.empty((ws_bytes,), dtype=torch.uint8, device=dev)
     post = (torch.empty((batch, B.R, B.n), dtype=torch.float32, device=dev)
             if want_posterior else None)
-    mbbp_decode(B, syndromes, llr, iters, alpha, rule, out["e_hat"], out["conv"], out["success"], ws,
-                iters_run=out["iters"], selected=out["selected"], posterior=post, stream=stream)
+    if schedule == SCHEDULE_FLOODING and decision == DECISION_FWS:
+        mbbp_decode(B, syndromes, llr, iters, alpha, rule, out["e_hat"], out["conv"], out["success"], ws,
+                    iters_run=out["iters"], selected=out["selected"], posterior=post, stream=stream)
+    else:
+        opt = Options(rule, float(alpha), schedule, decision)
+        mbbp_decode_ex(B, syndromes, llr, iters, opt, out["e_hat"], out["conv"], out["success"], ws,
+                       iters_run=out["iters"], selected=out["selected"], posterior=post, stream=stream)
     out["cand"] = ws[: batch * B.R * B.words * 4].view(torch.int32).view(batch, B.R, B.words)
     out["workspace"] = ws
     if want_posterior:

@@ -107,3 +107,13 @@ def test_missing_library_fails_loudly(tmp_path):
     res = subprocess.run([sys.executable, "-c", "import paper_2605_14170_gb300.mbbp"],
                          cwd=tmp_path, capture_output=True, text=True)
     assert res.returncode != 0 and "is not built" in res.stderr
+
+
+def test_random_sets_host_equals_oracle(lib):
+    """Random augmentation (Table II): the library's sets equal the oracle's."""
+    for m, sizes, seed in ((72, [3, 9, 1, 0, 72, 80], 5), (441, [40] * 64, 123), (1, [1, 0, 2], 9)):
+        a = lib.mbbp_random_sets(m, sizes, seed)
+        b = oracle.random_sets(m, sizes, seed)
+        assert [x.tolist() for x in a] == [x.tolist() for x in b]
+    with pytest.raises(lib.MBBPError):
+        lib.mbbp_random_sets(10, [-1], 1)
