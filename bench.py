@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bb144", choices=["bb144", "mixed", "learned"],
+    ap.add_argument("--workload", default="bb144", choices=["bb144", "mixed", "learned", "paper"],
                     help="bb144: the headline configuration; mixed: [[72]]/[[144]]/[[288]] in one "
                          "persistent graph-captured launch vs plain per-code launches")
     ap.add_argument("--shots", type=int, default=None,
@@ -379,10 +379,101 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_paper(args):
+    """The paper's own decoder setting on [[288,12,18]] (Section IV: serial
+    schedule, alpha = 0.875, 100 iterations; R = 20 subtree representations,
+    the partition count of Table II), X errors of code-capacity depolarizing
+    noise at p in {0.04, 0.06, 0.08}.  On the same shots: FWS (the paper's
+    rule) and LMS (classical MBBP), the matched random augmentation of
+    Table II, and flooding at alpha = 0.625.  ``value`` = shots/s of the
+    serial FWS decoder; per decoder: LER with its 95% interval, mean
+    iterations and shots/s."""
+    import torch
+
+    from paper_2605_14170_gb300 import learn, mbbp
+    from paper_2605_14170_gb300.inputs import named_code
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    c = named_code("bb288")
+    H = c.HZ
+    m, n = H.shape
+    Rp = 20
+    B = mbbp.mbbp_build_bases(H, Rp, SEED)
+    sizes = [len(x) for x in B.sets]
+    Br = mbbp.mbbp_build_bases_from_sets(H, mbbp.mbbp_random_sets(m, sizes, SEED + 7))
+    L = mbbp.mbbp_logicals_build(H, c.HX)
+    S = args.shots
+    W = (n + 31) // 32
+    ex = torch.empty((S, W), dtype=torch.int32, device=dev)
+    ez = torch.empty_like(ex)
+    syn = torch.empty((S, m), dtype=torch.uint8, device=dev)
+    decoders = {
+        "serial_fws": (B, 0.875, mbbp.SCHEDULE_SERIAL, mbbp.DECISION_FWS),
+        "serial_lms": (B, 0.875, mbbp.SCHEDULE_SERIAL, mbbp.DECISION_LMS),
+        "serial_fws_random_sets": (Br, 0.875, mbbp.SCHEDULE_SERIAL, mbbp.DECISION_FWS),
+        "flooding_fws_alpha0.625": (B, 0.625, mbbp.SCHEDULE_FLOODING, mbbp.DECISION_FWS),
+    }
+    edges = {k: torch.from_numpy(d[0].edges.astype(np.int64)).to(dev) for k, d in decoders.items()}
+    res = {k: {} for k in decoders}
+    tot_ms = {k: 0.0 for k in decoders}
+    tot_shots = 0
+    tot_work = {k: 0 for k in decoders}
+    ncalls = 0
+    with ClockSampler(0) as clk:
+        for ip, p in enumerate((0.04, 0.06, 0.08)):
+            pm = 2 * p / 3
+            llr = torch.full((n,), float(np.log((1 - pm) / pm)), dtype=torch.float32, device=dev)
+            fails = {k: torch.zeros(3, dtype=torch.int64, device=dev) for k in decoders}
+            iters_sum = {k: 0.0 for k in decoders}
+            for k in range(args.warmup + args.steps):
+                mbbp.mbbp_sample_errors(n, S, (ip * 1000 + k) * S, SEED, p, mbbp.NOISE_DEPOLARIZING, ex, ez)
+                mbbp.mbbp_syndrome(B, ex, syn)
+                for name, (BB, alpha, sch, dec) in decoders.items():
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    out = mbbp.decode(BB, syn, llr, ITERS, alpha, schedule=sch, decision=dec)
+                    e1.record()
+                    if k < args.warmup:
+                        continue
+                    mbbp.mbbp_judge(L, ex, out["e_hat"], None, fails[name])
+                    it = out["iters"].to(torch.int64) & 0xFFFF
+                    torch.cuda.synchronize()
+                    tot_ms[name] += e0.elapsed_time(e1)
+                    iters_sum[name] += float(it.float().mean().item())
+                    tot_work[name] += int((it.sum(0) * edges[name]).sum().item())
+                    ncalls += 1 if name == "serial_fws" else 0
+                if k >= args.warmup:
+                    tot_shots += S
+            for name in decoders:
+                f = fails[name].cpu().numpy()
+                kf = int(f[1] + f[2])
+                res[name][str(p)] = {"failures": kf, "ler": kf / (args.steps * S),
+                                     "ci95": learn.wilson(kf, args.steps * S),
+                                     "mean_iters": iters_sum[name] / args.steps}
+    shots_per_decoder = tot_shots
+    line = {
+        "metric": "decoded shots/s", "value": shots_per_decoder / (tot_ms["serial_fws"] / 1e3),
+        "unit": "shots/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms["serial_fws"] / (3 * args.steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "paper setting: [[288,12,18]] BB, X errors of depolarizing noise, p in "
+                               "{0.04,0.06,0.08}, R=20 subtree representations, serial schedule, "
+                               "alpha=0.875, 100 iters, FWS", "shots_per_p_per_step": S},
+        "decoders": {name: {"shots_per_s": shots_per_decoder / (tot_ms[name] / 1e3),
+                            "edge_updates_per_s": tot_work[name] / (tot_ms[name] / 1e3),
+                            "ler": res[name]} for name in decoders},
+        "random_set_sizes": sizes,
+        "gpu_launches": 3 * args.steps * (2 + 2 * len(decoders)),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.shots is None:
-        args.shots = {"mixed": 300_000, "learned": 100_000}.get(args.workload, 1_000_000)
+        args.shots = {"mixed": 300_000, "learned": 100_000, "paper": 200_000}.get(args.workload, 1_000_000)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -391,6 +482,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned(args)
+        return
+    if args.workload == "paper":
+        run_paper(args)
         return
 
     import torch

@@ -302,7 +302,7 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_decode_serial(const DecodeArgs& a, cudaStream_t s, int sm_count) {
+cudaError_t launch_decode_serial_generic(const DecodeArgs& a, cudaStream_t s, int sm_count) {
     const int K = a.B.DC;
     if (a.rule == MBBP_RULE_NMS) {
         if (K == 6) return launch_serial_t<6, MBBP_RULE_NMS>(a, s, sm_count);

@@ -354,6 +354,12 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     std::vector<uint16_t> vslot;
     std::vector<int32_t> rows(R), edges(R);
     std::vector<uint2> evar((size_t)R * K * MP, make_uint2(0, 0));
+    // chunked serial path (widths 6 and 8): per-edge and per-variable slot
+    // descriptors with byte offsets, padded with the -0.0f slot
+    const bool chunked = (K == 6 || K == 8);
+    const uint32_t negz = 4u * (uint32_t)(K * MP);
+    std::vector<uint4> edesc(chunked ? (size_t)R * K * MP : 0, make_uint4(0, 0, 0, 0));
+    std::vector<uint4> vdesc3(chunked ? (size_t)R * n : 0, make_uint4(0, 0, 0, 0));
     B->lorder.assign((size_t)R * MP, 0);
     B->lptr.assign((size_t)R * (MP + 1), 0);
     B->nlayers.assign(R, 0);
@@ -376,6 +382,27 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         for (int v = 0; v < n; ++v) ord[v] = v;
         std::stable_sort(ord.begin(), ord.end(),
                          [&](int a, int b) { return vl[a].size() < vl[b].size(); });
+        if (chunked) {
+            auto pack = [](const uint32_t* o) {
+                return make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
+                                  o[6] | (o[7] << 16));
+            };
+            for (int v = 0; v < n; ++v) {
+                uint32_t o[8];
+                for (int i = 0; i < 8; ++i) o[i] = i < (int)vl[v].size() ? 4u * vl[v][i] : negz;
+                vdesc3[(size_t)t * n + v] = pack(o);
+                for (int k = 0; k < (int)vl[v].size(); ++k) {
+                    const uint32_t slot = vl[v][k];
+                    uint32_t e[8];
+                    e[0] = (uint32_t)v;
+                    int c = 1;
+                    for (int i = 0; i < (int)vl[v].size(); ++i)
+                        if (i != k) e[c++] = 4u * vl[v][i];
+                    while (c < 8) e[c++] = negz;
+                    edesc[(size_t)t * K * MP + slot] = pack(e);
+                }
+            }
+        }
         std::vector<uint2> vstart(n);
         for (int p = 0; p < n; ++p) {
             const int v = ord[p];
@@ -503,7 +530,9 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     const size_t o_lptr = o_lrows + align256(lrows16.size() * 2);
     const size_t o_nlayers = o_lptr + align256(lptr16.size() * 2);
     const size_t o_evar = o_nlayers + align256((size_t)R * 4);
-    const size_t total = o_evar + align256(evar.size() * sizeof(uint2));
+    const size_t o_edesc = o_evar + align256(evar.size() * sizeof(uint2));
+    const size_t o_vdesc3 = o_edesc + align256(edesc.size() * sizeof(uint4));
+    const size_t total = o_vdesc3 + align256(vdesc3.size() * sizeof(uint4));
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
     if (e == cudaSuccess) e = cudaMalloc(&B->dmem, total);
@@ -527,6 +556,8 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         {o_lptr, lptr16.data(), lptr16.size() * 2},
         {o_nlayers, B->nlayers.data(), (size_t)R * 4},
         {o_evar, evar.data(), evar.size() * sizeof(uint2)},
+        {o_edesc, edesc.data(), edesc.size() * sizeof(uint4)},
+        {o_vdesc3, vdesc3.data(), vdesc3.size() * sizeof(uint4)},
     };
     for (const Copy& c : copies) {
         if (c.bytes == 0) continue;
@@ -558,6 +589,8 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     d.lptr = reinterpret_cast<const uint16_t*>(base + o_lptr);
     d.nlayers = reinterpret_cast<const int32_t*>(base + o_nlayers);
     d.evar = reinterpret_cast<const uint2*>(base + o_evar);
+    d.edesc = chunked ? reinterpret_cast<const uint4*>(base + o_edesc) : nullptr;
+    d.vdesc3 = chunked ? reinterpret_cast<const uint4*>(base + o_vdesc3) : nullptr;
     *out = B;
     return MBBP_OK;
 }
@@ -742,7 +775,9 @@ mbbp_status mbbp_syndrome(const mbbp_bases* B, int batch, const uint32_t* e, uin
 
 size_t mbbp_decode_workspace_size(const mbbp_bases* B, int batch) {
     if (!B || batch < 0) return 0;
-    return align256((size_t)batch * B->R * B->W * 4) + 256;
+    // candidates, then the work counter (8 bytes) and one shot counter per
+    // representation (4 bytes each)
+    return align256((size_t)batch * B->R * B->W * 4) + 512;
 }
 
 mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes,
@@ -803,7 +838,9 @@ mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndro
     a.io.iters_run = iters_run;
     a.io.post = posterior;
     a.total_items = (unsigned long long)batch * B->R;
-    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    a.rep_counter = reinterpret_cast<unsigned int*>(a.counter + 1);
+    const size_t counter_bytes = sizeof(unsigned long long) + sizeof(unsigned int) * (size_t)B->R;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, counter_bytes, s);
     if (e == cudaSuccess)
         e = opt->schedule == MBBP_SCHEDULE_SERIAL ? launch_decode_serial(a, s, B->sm_count)
                                                   : launch_decode(a, s, B->sm_count);

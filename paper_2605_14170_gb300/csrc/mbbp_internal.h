@@ -49,6 +49,13 @@ struct DevBases {
     const uint16_t* lptr;     // [R][MP+1]
     const int32_t* nlayers;   // [R]
     const uint2* evar;        // [R][DC*MP]
+    // Serial schedule, widths 6 and 8 (null otherwise): per edge slot,
+    // x = variable | first other edge << 16 and y/z/w = further other edges of
+    // the variable (byte offsets of their slots, ascending row, padded with
+    // the offset 4 * DC * MP of a -0.0f slot); per variable, its 8 slot byte
+    // offsets (ascending row, padded the same way).
+    const uint4* edesc;       // [R][DC*MP]
+    const uint4* vdesc3;      // [R][n]
 };
 
 // Bank rotation of edge position j in the small-code layout.
@@ -79,6 +86,7 @@ struct DecodeArgs {
     int rule;
     unsigned long long* counter;
     unsigned long long total_items;
+    unsigned int* rep_counter;  // [R] next shot of each representation (serial slot path)
 };
 
 struct FwsArgs {
@@ -154,6 +162,7 @@ cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, size_t c
 // Launchers (decode.cu, decode_small.cu, aux.cu).  They return cudaGetLastError().
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_decode_serial(const DecodeArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_decode_serial_generic(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_decode_small(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_fws(const FwsArgs& a, cudaStream_t s);
 size_t decode_smem_bytes(const DevBases& B, int warps);
