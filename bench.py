@@ -380,10 +380,10 @@ def run_learned(args):
 
 
 def run_paper(args):
-    """The paper's own decoder setting on [[288,12,18]] (Section IV: serial
-    schedule, alpha = 0.875, 100 iterations; R = 20 subtree representations,
-    the partition count of Table II), X errors of code-capacity depolarizing
-    noise at p in {0.04, 0.06, 0.08}.  On the same shots: FWS (the paper's
+    """The paper's own decoder setting on [[288,12,18]] (Section IV: binary
+    symmetric channel of independent X errors at p_x in {0.04, 0.06, 0.08},
+    serial schedule, alpha = 0.875, 100 iterations; R = 20 subtree
+    representations, the partition count of Table II).  On the same shots: FWS (the paper's
     rule) and LMS (classical MBBP), the matched random augmentation of
     Table II, and flooding at alpha = 0.625.  ``value`` = shots/s of the
     serial FWS decoder; per decoder: LER with its 95% interval, mean
@@ -406,7 +406,6 @@ def run_paper(args):
     S = args.shots
     W = (n + 31) // 32
     ex = torch.empty((S, W), dtype=torch.int32, device=dev)
-    ez = torch.empty_like(ex)
     syn = torch.empty((S, m), dtype=torch.uint8, device=dev)
     decoders = {
         "serial_fws": (B, 0.875, mbbp.SCHEDULE_SERIAL, mbbp.DECISION_FWS),
@@ -422,12 +421,11 @@ def run_paper(args):
     ncalls = 0
     with ClockSampler(0) as clk:
         for ip, p in enumerate((0.04, 0.06, 0.08)):
-            pm = 2 * p / 3
-            llr = torch.full((n,), float(np.log((1 - pm) / pm)), dtype=torch.float32, device=dev)
+            llr = torch.full((n,), float(np.log((1 - p) / p)), dtype=torch.float32, device=dev)
             fails = {k: torch.zeros(3, dtype=torch.int64, device=dev) for k in decoders}
             iters_sum = {k: 0.0 for k in decoders}
             for k in range(args.warmup + args.steps):
-                mbbp.mbbp_sample_errors(n, S, (ip * 1000 + k) * S, SEED, p, mbbp.NOISE_DEPOLARIZING, ex, ez)
+                mbbp.mbbp_sample_errors(n, S, (ip * 1000 + k) * S, SEED, p, mbbp.NOISE_BSC, ex, None)
                 mbbp.mbbp_syndrome(B, ex, syn)
                 for name, (BB, alpha, sch, dec) in decoders.items():
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -457,7 +455,7 @@ def run_paper(args):
         "unit": "shots/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot_ms["serial_fws"] / (3 * args.steps), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "paper setting: [[288,12,18]] BB, X errors of depolarizing noise, p in "
+        "config": {"workload": "paper setting: [[288,12,18]] BB, independent X errors (BSC) at p_x in "
                                "{0.04,0.06,0.08}, R=20 subtree representations, serial schedule, "
                                "alpha=0.875, 100 iters, FWS", "shots_per_p_per_step": S},
         "decoders": {name: {"shots_per_s": shots_per_decoder / (tot_ms[name] / 1e3),

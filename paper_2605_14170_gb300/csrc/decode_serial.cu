@@ -24,11 +24,11 @@ decode_serial_chunk_kernel(const DecodeArgs a) {
     unsigned char* area = smem + hcol_bytes + warp * L.bytes;
     for (int i = threadIdx.x; i < DC * B.mpad; i += blockDim.x) hcol_s[i] = __ldg(B.hcol + i);
     __syncthreads();
-    // warps start spread over the representations and move on to the next
-    // one when the shots of theirs run out
-    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    // the warps of a block work on the same representation (its edge
+    // descriptors stay in L1); blocks start spread over the representations
+    // and move on to the next one when the shots of theirs run out
     for (int k = 0; k < R; ++k) {
-        const int b = (gw + k) % R;
+        const int b = (int)((blockIdx.x + k) % (unsigned)R);
         serial_bp::run_rep<DC, NO, NV, RULE, REG, CS>(B, a.io, b, a.rep_counter + b, area, hcol_s);
     }
 }
