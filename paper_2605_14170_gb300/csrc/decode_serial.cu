@@ -1,8 +1,8 @@
 // Serial-schedule launches (Section II-B).  Kernel widths 6 and 8 use the
 // slot path of bp_serial.cuh: a persistent grid whose warps pull shots of
 // one representation at a time from per-representation counters and decode
-// CS of them at once (CS = 4, 2 or 1, the largest whose per-warp shared
-// memory lets 8-warp blocks run two to an SM, else one).  Width 12 uses the
+// CS of them at once (CS = 4, 2 or 1, the largest that leaves about half of
+// the SM's shared memory to L1 with two 8-warp blocks per SM).  Width 12 uses the
 // one-item-per-warp generic serial kernel.
 #include "bp_serial.cuh"
 
@@ -51,14 +51,18 @@ cudaError_t launch_t(const DecodeArgs& a, cudaStream_t s, int sm_count, int warp
 
 template <int DC, int NO, int NV, int RULE, bool REG>
 cudaError_t launch_cs(const DecodeArgs& a, cudaStream_t s, int sm_count) {
-    // the largest CS whose 8-warp block fits twice in 200 KB, else the
-    // largest warp count at CS = 1 that fits once
+    // the largest CS whose 8-warp block fits twice in about half of the
+    // SM's shared memory (the rest stays L1, which holds the edge
+    // descriptors of the blocks' representations), else the largest warp
+    // count at CS = 1 that fits once
     const size_t hb = (size_t)generic_bp::align16(DC * a.B.mpad * 2);
-    const size_t budget2 = 100 * 1024, budget1 = 200 * 1024;
+    const size_t budget2 = 56 * 1024, budget1 = 200 * 1024;
     if (hb + kSerialWarps * (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 4).bytes <= budget2)
         return launch_t<DC, NO, NV, RULE, REG, 4>(a, s, sm_count, kSerialWarps);
     if (hb + kSerialWarps * (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 2).bytes <= budget2)
         return launch_t<DC, NO, NV, RULE, REG, 2>(a, s, sm_count, kSerialWarps);
+    if (hb + kSerialWarps * (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 1).bytes <= budget2)
+        return launch_t<DC, NO, NV, RULE, REG, 1>(a, s, sm_count, kSerialWarps);
     int warps = kSerialWarps;
     const size_t per = (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 1).bytes;
     while (warps > 1 && hb + warps * per > budget1) --warps;
