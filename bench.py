@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bb144", choices=["bb144", "mixed", "learned", "paper"],
+    ap.add_argument("--workload", default="bb144", choices=["bb144", "mixed", "learned", "paper", "wms"],
                     help="bb144: the headline configuration; mixed: [[72]]/[[144]]/[[288]] in one "
                          "persistent graph-captured launch vs plain per-code launches")
     ap.add_argument("--shots", type=int, default=None,
@@ -363,6 +363,14 @@ def run_learned(args):
 
     ms_plain = timed(lambda: mbbp.decode(B, syn, llr, ITERS, ALPHA))
     ms_learned = timed(lambda: mbbp.wms_decode(B, syn, llr, ITERS, w, g))
+    # the same recipe on [[144,12,12]] with R = 8, where the LER is high
+    # enough for the weights to make a measurable difference
+    c2 = named_code("bb144")
+    B2 = mbbp.mbbp_build_bases(c2.HZ, 8, SEED)
+    L2 = mbbp.mbbp_logicals_build(c2.HZ, c2.HX)
+    w2, g2, hist2 = learn.train_wms(B2, 0.05, T=25, ckpt=5, batch=2048, steps=150, lr=1e-3, L=L2,
+                                    val_shots=30000, val_every=25, log_every=0)
+    res2 = {str(pp): learn.compare_ler(B2, L2, w2, g2, pp, 200_000, ITERS) for pp in (0.03, 0.04, 0.05, 0.06)}
     line = {
         "metric": "decoded shots/s", "value": shots / (ms_learned / 1e3), "unit": "shots/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True,
@@ -375,6 +383,11 @@ def run_learned(args):
         "selected_step": min(hist, key=lambda h: (h[2] if h[2] is not None else 1 << 60))[0],
         "ler": {p: {"plain": r["plain"]["ler"], "plain_ci95": r["plain"]["ci95"],
                     "learned": r["learned"]["ler"], "learned_ci95": r["learned"]["ci95"]} for p, r in res.items()},
+        "bb144_r8": {"train": "150 steps x 2048 shots at p=0.05, validation-selected",
+                     "selected_step": min(hist2, key=lambda h: (h[2] if h[2] is not None else 1 << 60))[0],
+                     "ler": {p: {"plain_failures": r["plain"]["failures"], "learned_failures": r["learned"]["failures"],
+                                 "shots": r["shots"], "plain_ci95": r["plain"]["ci95"],
+                                 "learned_ci95": r["learned"]["ci95"]} for p, r in res2.items()}},
     }
     print(json.dumps(line), flush=True)
 
@@ -468,6 +481,92 @@ def run_paper(args):
     print(json.dumps(line), flush=True)
 
 
+def run_wms(args):
+    """One training step of differentiable weighted min-sum per bench step on
+    [[144,12,12]] (R = 8 subtree representations, T = 25 unrolled flooding
+    iterations, per-edge per-iteration weights and damping, checkpoint
+    every 5 iterations, batch 4096 depolarizing X errors at p = 0.06, BCE of
+    every iteration's posterior): sample + syndrome + forward + hand-written
+    adjoint + two Adam steps, all in the library's kernels.  ``value`` =
+    training syndromes/s; the forward and backward kernels are timed
+    separately with CUDA events."""
+    import torch
+
+    from paper_2605_14170_gb300 import mbbp
+    from paper_2605_14170_gb300.inputs import named_code
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    c = named_code("bb144")
+    B = mbbp.mbbp_build_bases(c.HZ, 8, SEED)
+    T, ckpt, batch, p = 25, 5, 4096, 0.06
+    n, W = c.n, (c.n + 31) // 32
+    w, g = mbbp.wms_params(B, T, alpha=ALPHA, device=dev)
+    mw, vw, mg, vg = (torch.zeros_like(w) for _ in range(4))
+    gw, gg = torch.zeros_like(w), torch.zeros_like(g)
+    ex = torch.empty((batch, W), dtype=torch.int32, device=dev)
+    ez = torch.empty_like(ex)
+    syn = torch.empty((batch, B.m), dtype=torch.uint8, device=dev)
+    post = torch.empty((batch, B.R, n), dtype=torch.float32, device=dev)
+    loss = torch.empty((batch, B.R), dtype=torch.float32, device=dev)
+    ws_bytes = mbbp.mbbp_wms_workspace_size(B, batch, T, ckpt)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    pm = 2 * p / 3
+    llr = torch.full((n,), float(np.log((1 - pm) / pm)), dtype=torch.float32, device=dev)
+    scale = 1.0 / (batch * B.R * n)
+    ev = []
+
+    def step(k, record):
+        mbbp.mbbp_sample_errors(n, batch, k * batch, SEED, p, mbbp.NOISE_DEPOLARIZING, ex, ez)
+        mbbp.mbbp_syndrome(B, ex, syn)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        mbbp.mbbp_wms_forward(B, syn, llr, T, w, g, ckpt, ex, scale, post, loss, ws, all_iters=True)
+        e[1].record()
+        gw.zero_()
+        gg.zero_()
+        mbbp.mbbp_wms_backward(B, syn, llr, T, w, g, ckpt, ex, scale, post, gw, gg, ws, all_iters=True)
+        e[2].record()
+        mbbp.mbbp_adam_step(w, gw, mw, vw, 1e-3, 0.9, 0.999, 1e-8, k + 1, 0.0, 2.0)
+        mbbp.mbbp_adam_step(g, gg, mg, vg, 1e-3, 0.9, 0.999, 1e-8, k + 1, 0.0, 0.9)
+        if record:
+            ev.append(e)
+
+    for k in range(args.warmup):
+        step(k, False)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        t0.record()
+        for k in range(args.steps):
+            step(args.warmup + k, True)
+        t1.record()
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    fwd = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+    bwd = statistics.mean(b.elapsed_time(c_) for _, b, c_ in ev)
+    E = int(B.edges.sum())
+    upd = batch * T * E  # forward message updates per step (every edge of every representation)
+    ck_bytes = batch * B.R * int(B.edges.max()) * 4 * ((T - 1) // ckpt)
+    full_bytes = batch * B.R * int(B.edges.max()) * 4 * T
+    line = {
+        "metric": "training syndromes/s", "value": args.steps * batch / (ms / 1e3), "unit": "syndromes/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "weighted min-sum training step: [[144,12,12]] R=8, T=25 unrolled iterations, "
+                               "per-edge per-iteration weights + damping, checkpoint every 5, batch 4096, "
+                               "depolarizing p=0.06, BCE of every iteration", "batch": batch, "T": T, "ckpt": ckpt},
+        "forward_ms": fwd, "backward_ms": bwd,
+        "forward_edge_updates_per_s": upd / (fwd / 1e3),
+        "workspace_bytes": ws_bytes, "message_bytes_checkpointed": ck_bytes,
+        "message_bytes_without_checkpoints": full_bytes,
+        "loss": float(loss.sum().item()),
+        "gpu_launches": args.steps * 8,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.shots is None:
@@ -483,6 +582,9 @@ def main():
         return
     if args.workload == "paper":
         run_paper(args)
+        return
+    if args.workload == "wms":
+        run_wms(args)
         return
 
     import torch
