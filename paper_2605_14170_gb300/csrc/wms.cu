@@ -233,7 +233,9 @@ wms_forward_kernel(const WmsArgs a) {
     }
 }
 
-template <int DC, int DV>
+// SMEM_ST: the segment's recomputed states sit in shared memory after the
+// warp's other arrays (small codes); otherwise in the warp's global buffer.
+template <int DC, int DV, bool SMEM_ST>
 __global__ void __launch_bounds__(kWmsWarps * 32)
 wms_backward_kernel(const WmsArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -243,8 +245,11 @@ wms_backward_kernel(const WmsArgs a) {
     const int MP = B.MP, n = B.n, m_rows = B.m, R = B.R;
     const WmsLayout L = wms_layout(DC, MP, n, a.ckpt);
     const size_t gwarp = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    float* states = a.seg_buf + gwarp * (size_t)a.ckpt * L.S;  // [ckpt][S], this warp's
-    float* q = reinterpret_cast<float*>(smem + warp * L.bwd_bytes);
+    const size_t st_bytes = SMEM_ST ? (size_t)a.ckpt * L.S * 4 : 0;
+    unsigned char* wbase = smem + warp * (L.bwd_bytes + st_bytes);
+    float* states = SMEM_ST ? reinterpret_cast<float*>(wbase + L.bwd_bytes)
+                            : a.seg_buf + gwarp * (size_t)a.ckpt * L.S;  // [ckpt][S], this warp's
+    float* q = reinterpret_cast<float*>(wbase);
     float* gm = q + L.S;
     float* gmp = gm + L.S;
     float* gq = gmp + L.S;
@@ -337,26 +342,35 @@ wms_backward_kernel(const WmsArgs a) {
                     if (r >= Mb) continue;
                     const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
                     const int e0 = __ldg(rp + r);
-                    float qq[DC], gacc[DC];
+                    float qq[DC];
 #pragma unroll
-                    for (int j = 0; j < DC; ++j) {
-                        qq[j] = (j < deg) ? q[j * MP + r] : MBBP_LMAX;
-                        gacc[j] = 0.0f;
+                    for (int j = 0; j < DC; ++j) qq[j] = (j < deg) ? q[j * MP + r] : MBBP_LMAX;
+                    // the smallest and second smallest |q| below LMAX with
+                    // their lowest-index positions, and the sign parity: the
+                    // min over the edges other than j is (min1, a1) unless
+                    // j == a1, then (min2, a2)
+                    float min1 = MBBP_LMAX, min2 = MBBP_LMAX;
+                    int a1 = -1, a2 = -1;
+                    uint32_t par = (sb >> k) & 1u;
+#pragma unroll
+                    for (int u = 0; u < DC; ++u) {
+                        if (u >= deg) continue;
+                        const float x = fabsf(qq[u]);
+                        if (x < min1) {
+                            min2 = min1; a2 = a1;
+                            min1 = x; a1 = u;
+                        } else if (x < min2) {
+                            min2 = x; a2 = u;
+                        }
+                        par ^= (qq[u] < 0.f) ? 1u : 0u;
                     }
-                    const uint32_t s = (sb >> k) & 1u;
+                    float G1 = 0.0f, G2 = 0.0f;  // dL/d|min| routed to a1 / a2
 #pragma unroll
                     for (int j = 0; j < DC; ++j) {
                         if (j >= deg) continue;
-                        float mn = MBBP_LMAX;
-                        int arg = -1;
-                        uint32_t neg = s;
-#pragma unroll
-                        for (int u = 0; u < DC; ++u) {
-                            if (u == j || u >= deg) continue;
-                            const float x = fabsf(qq[u]);
-                            if (x < mn) { mn = x; arg = u; }
-                            neg ^= (qq[u] < 0.f) ? 1u : 0u;
-                        }
+                        const bool own = (j == a1);
+                        const float mn = own ? min2 : min1;
+                        const uint32_t neg = par ^ ((qq[j] < 0.f) ? 1u : 0u);
                         const float sgn = neg ? -1.0f : 1.0f;
                         const float ww = __ldg(wt + e0 + j), gg = __ldg(gt + e0 + j);
                         const float gmj = gm[j * MP + r];
@@ -365,13 +379,18 @@ wms_backward_kernel(const WmsArgs a) {
                         atomicAdd(gwt + e0 + j, gmj * (1.0f - gg) * sgn * mn);
                         gmp[j * MP + r] = gmj * gg;
                         const float gmn = gmj * (1.0f - gg) * ww * sgn;
-#pragma unroll
-                        for (int u = 0; u < DC; ++u)
-                            if (u == arg) gacc[u] += gmn * (qq[u] < 0.f ? -1.0f : 1.0f);
+                        if (own) G2 += gmn;
+                        else G1 += gmn;
                     }
 #pragma unroll
-                    for (int j = 0; j < DC; ++j)
-                        if (j < deg) gq[j * MP + r] = gacc[j];
+                    for (int j = 0; j < DC; ++j) {
+                        if (j >= deg) continue;
+                        const float sq = (qq[j] < 0.f) ? -1.0f : 1.0f;
+                        float gj = 0.0f;
+                        if (j == a1) gj = G1 * sq;
+                        if (j == a2) gj = G2 * sq;
+                        gq[j * MP + r] = gj;
+                    }
                 }
                 __syncwarp();
                 if (t >= 2) {
@@ -420,13 +439,18 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ gra
 template <int K>
 cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count) {
     const WmsLayout L = wms_layout(K, a.B.MP, a.B.n, a.ckpt);
-    const size_t per_warp = backward ? L.bwd_bytes : L.fwd_bytes;
+    // backward: keep the segment states in shared memory when four warps'
+    // worth fits in about half of an SM's shared memory
+    const size_t st_bytes = (size_t)a.ckpt * L.S * 4;
+    const bool smem_st = backward && (size_t)kWmsWarps * (L.bwd_bytes + st_bytes) <= 110 * 1024;
+    const size_t per_warp = backward ? L.bwd_bytes + (smem_st ? st_bytes : 0) : L.fwd_bytes;
     int warps = kWmsWarps;
     while (warps > 1 && warps * per_warp > 200 * 1024) --warps;
     if (per_warp > 200 * 1024) return cudaErrorInvalidConfiguration;
     const size_t smem = warps * per_warp;
-    const void* kern = backward ? reinterpret_cast<const void*>(wms_backward_kernel<K, K>)
-                                : reinterpret_cast<const void*>(wms_forward_kernel<K, K>);
+    const void* kern = !backward ? reinterpret_cast<const void*>(wms_forward_kernel<K, K>)
+                       : smem_st ? reinterpret_cast<const void*>(wms_backward_kernel<K, K, true>)
+                                 : reinterpret_cast<const void*>(wms_backward_kernel<K, K, false>);
     int per_sm = 0;
     cudaError_t e = prepare_kernel(kern, warps * 32, smem, &per_sm);
     if (e != cudaSuccess) return e;
@@ -437,8 +461,10 @@ cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm
         const unsigned long long cap = kWmsMaxWarps / warps;
         if (grid > cap) grid = cap;
     }
-    if (backward)
-        wms_backward_kernel<K, K><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    if (backward && smem_st)
+        wms_backward_kernel<K, K, true><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    else if (backward)
+        wms_backward_kernel<K, K, false><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     else
         wms_forward_kernel<K, K><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     return cudaGetLastError();
