@@ -590,7 +590,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2605_14170_gb300 import mbbp
+    from paper_2605_14170_gb300 import mbbp, shard
     from paper_2605_14170_gb300.inputs import named_code
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -635,7 +635,7 @@ def main():
         nonlocal launches_per_step
         launches = 0
         for ip, p in enumerate(P_LIST):
-            first = ((k * world + rank) * len(P_LIST) + ip) * S
+            first = shard.first_shot(k, rank, world, ip, len(P_LIST), S)
             mbbp.mbbp_sample_errors(n, S, first, SEED, p, mbbp.NOISE_DEPOLARIZING, ex, ez)
             launches += 1
             for key, B, L, e, fl in (("Z", BZ, LZ, ex, fail_x), ("X", BX, LX, ez, fail_z)):
@@ -674,13 +674,8 @@ def main():
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = t0.elapsed_time(t1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(counts)
-        dist.all_reduce(work)
-    ms = float(ms_t.item())
+    ms = shard.max_over_ranks(dist, t0.elapsed_time(t1), dev)
+    shard.reduce_counters(dist, counts, work)
     shots_total = args.steps * len(P_LIST) * S * world
     value = shots_total / (ms / 1000.0)
     edge_updates = int(work.item())
@@ -794,9 +789,9 @@ def run_e2e(args, mbbp, BZ, BX, llrs, S, dev, stream, rank, world):
     dt = time.perf_counter() - t0
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([dt], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+
+        from paper_2605_14170_gb300 import shard
+        dt = shard.max_over_ranks(dist, dt, dev)
     shots = args.steps * len(P_LIST) * S * world
     return {"value": shots / dt, "unit": "shots/s",
             "h2d_bytes_per_step": len(P_LIST) * 2 * S * m,
