@@ -628,6 +628,9 @@ def main():
     fail_z = torch.empty((S,), dtype=torch.uint8, device=dev)
     counts = torch.zeros((len(P_LIST), 3, 3), dtype=torch.int64, device=dev)  # p, type(X,Z,any), code
     work = torch.zeros((), dtype=torch.int64, device=dev)
+    # per p: sum over (shot, representation) of K, and sum over shots of the
+    # largest K of the shot's representations (the latency term), X and Z
+    kstats = torch.zeros((len(P_LIST), 2), dtype=torch.int64, device=dev)
     dec_events = []
     launches_per_step = 0
 
@@ -651,7 +654,10 @@ def main():
                     dec_events.append((ev0, ev1, key))
                 mbbp.mbbp_judge(L, e, e_hat, fl, counts[ip, 0 if key == "Z" else 1])
                 launches += 4  # syndrome, BP, FWS, judge
-                work.add_(((iters.to(torch.int64) & 0xFFFF).sum(0) * edges[key]).sum())
+                it64 = iters.to(torch.int64) & 0xFFFF
+                work.add_((it64.sum(0) * edges[key]).sum())
+                kstats[ip, 0] += it64.sum()
+                kstats[ip, 1] += it64.max(1).values.sum()
             # any-type failure for the combined logical error rate
             counts[ip, 2, 1] += ((fail_x != 0) | (fail_z != 0)).sum()
         launches_per_step = launches
@@ -661,6 +667,7 @@ def main():
     torch.cuda.synchronize()
     counts.zero_()
     work.zero_()
+    kstats.zero_()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -675,7 +682,7 @@ def main():
     if world > 1:
         dist.barrier()
     ms = shard.max_over_ranks(dist, t0.elapsed_time(t1), dev)
-    shard.reduce_counters(dist, counts, work)
+    shard.reduce_counters(dist, counts, work, kstats)
     shots_total = args.steps * len(P_LIST) * S * world
     value = shots_total / (ms / 1000.0)
     edge_updates = int(work.item())
@@ -689,6 +696,7 @@ def main():
     peak_ops = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
     achieved_ops = OPS_PER_EDGE_UPDATE * edge_per_launch / (dec_avg_ms / 1000.0)
     cnt = counts.cpu().numpy()
+    ks = kstats.cpu().numpy()
     ler = {str(p): {"x": float(cnt[i, 0, 2] + cnt[i, 0, 1]) / (args.steps * S * world),
                     "z": float(cnt[i, 1, 2] + cnt[i, 1, 1]) / (args.steps * S * world),
                     "any": float(cnt[i, 2, 1]) / (args.steps * S * world)} for i, p in enumerate(P_LIST)}
@@ -714,7 +722,12 @@ def main():
                              f"{S * m / 1e6:.0f} MB syndromes, {ws.numel() / 1e6:.0f} MB workspace, "
                              f"{S * n / 1e6:.0f} MB estimates)"},
             "edge_updates_per_s": edge_updates / (ms / 1000.0),
+            "edge_updates_per_shot": edge_updates / shots_total,
+            "edge_updates_per_shot_dense_bound": 2 * R * float(np.mean(BZ.edges)) * ITERS,
             "decoded_syndromes_per_s": 2 * value,
+            "iterations": {str(p): {"mean_K": float(ks[i, 0]) / (2 * args.steps * S * world * R),
+                                    "mean_K_max_per_shot": float(ks[i, 1]) / (2 * args.steps * S * world)}
+                           for i, p in enumerate(P_LIST)},
             "ler": ler,
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved_ops / peak_ops,

@@ -165,6 +165,44 @@ def test_checkpoint_interval_does_not_change_gradients():
         torch.testing.assert_close(gg, res[0][2], rtol=1e-5, atol=1e-6)
 
 
+def test_segment_states_in_global_memory_match_shared_memory():
+    """[[144,12,12]] with checkpoint 2 keeps the backward segment states in
+    shared memory; checkpoint 12 (one segment of 12 iterations) does not fit
+    and keeps them in the per-warp global buffer.  Both give the gradients of
+    the FP64 oracle adjoint and of each other."""
+    import torch
+    from paper_2605_14170_gb300 import mbbp
+    shots, T = 6, 12
+    H, B, s, ex, mu, w, g, t = _setup(code="bb144", R=2, shots=shots, T=T, seed=6)
+    n = H.shape[1]
+    scale = 1.0 / (shots * B.R * n)
+    res = []
+    for ckpt in (2, 12):
+        post = torch.empty((shots, B.R, n), dtype=torch.float32, device="cuda")
+        ws = torch.empty(mbbp.mbbp_wms_workspace_size(B, shots, T, ckpt), dtype=torch.uint8, device="cuda")
+        mbbp.mbbp_wms_forward(B, t["s"], t["mu"], T, t["w"], t["g"], ckpt, t["e"], scale, post, None, ws,
+                              all_iters=True)
+        gw = torch.zeros_like(t["w"])
+        gg = torch.zeros_like(t["g"])
+        mbbp.mbbp_wms_backward(B, t["s"], t["mu"], T, t["w"], t["g"], ckpt, t["e"], scale, post, gw, gg, ws,
+                               all_iters=True)
+        torch.cuda.synchronize()
+        res.append((gw.cpu().numpy().astype(np.float64), gg.cpu().numpy().astype(np.float64)))
+    w32, g32, mu32 = (x.astype(np.float32).astype(np.float64) for x in (w, g, mu))
+    gw_ref, gg_ref = np.zeros_like(w32), np.zeros_like(g32)
+    for shot in range(shots):
+        for b in range(B.R):
+            Ht, st, wb, gb, Eb = _oracle_item(H, B, s, mu32, w32, g32, ex, shot, b, scale)
+            _, gwb, ggb = oracle.wms_backward(Ht, st, mu32, wb, gb, ex[shot], scale, all_iters=True)
+            gw_ref[b][:, :Eb] += gwb
+            gg_ref[b][:, :Eb] += ggb
+    for gw, gg in res:
+        for got, ref in ((gw, gw_ref), (gg, gg_ref)):
+            assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
+    np.testing.assert_allclose(res[0][0], res[1][0], rtol=1e-4, atol=1e-9)
+    np.testing.assert_allclose(res[0][1], res[1][1], rtol=1e-4, atol=1e-9)
+
+
 def test_autograd_function_and_adam():
     import torch
     from paper_2605_14170_gb300 import mbbp
