@@ -287,8 +287,10 @@ void mbbp_plan_free(mbbp_plan* P);
 size_t mbbp_plan_workspace_size(const mbbp_plan* P, const int32_t* batches);
 
 /* Decode io[c] (host array of n_codes entries) with code c of the plan: one
- * persistent BP launch over every (code, shot chunk, representation) work
- * item, then FWS per code.  Outputs are identical to one mbbp_decode per
+ * persistent BP launch per kernel body the plan uses (small-code path,
+ * generic path; each with its own register budget) over every (code, shot
+ * chunk, representation) work item of that body, then FWS per code.
+ * Outputs are identical to one mbbp_decode per
  * code.  Only kernel launches and a memset are enqueued, so the call can be
  * captured into a CUDA graph (after the first call with the same plan, shapes
  * and block size, which sets kernel attributes).  Workspace: as mbbp_decode,

@@ -1,9 +1,13 @@
-// Persistent mixed-batch BP kernel: one launch decodes the shots of several
-// codes (each with its own R representations and sizes).  Warps pull work
-// items (code, chunk of shots, representation) from one global counter, in
-// the order the plan chose (heaviest codes first by default), and run the
-// small-code path (bp_small.cuh) or the generic path (bp_generic.cuh) that the
-// plan assigned to the code.  Every per-code argument travels in the kernel
+// Persistent mixed-batch BP kernels: one launch decodes the shots of several
+// codes (each with its own R representations and sizes) that the plan
+// assigned to one kernel body — the small-code path (bp_small.cuh) or the
+// generic path (bp_generic.cuh); a plan with both kinds issues one launch of
+// each on the stream.  Each body gets its own register budget: the small
+// path needs about 128 registers per thread, the generic path about 40, and
+// sharing one kernel would hold the generic items to the small path's
+// occupancy.  Warps pull work items (code, chunk of shots, representation)
+// from the launch's counter, in the order the plan chose (heaviest codes
+// first by default).  Every per-code argument travels in the kernel
 // parameters, so a captured CUDA graph holds them by value.
 #include "bp_generic.cuh"
 #include "bp_small.cuh"
@@ -11,9 +15,8 @@
 namespace mbbp {
 namespace {
 
-template <int RULE>
-__global__ void __launch_bounds__(kMixedMaxWarps * 32, 2)
-mixed_kernel(const MixedArgs a) {
+template <int RULE, int KIND>
+__device__ __forceinline__ void mixed_body(const MixedArgs& a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -32,7 +35,7 @@ mixed_kernel(const MixedArgs a) {
         const int b = (int)(l - (unsigned long long)sblock * R);
         const int s0 = sblock * mc.chunk;
         const int s1 = min(mc.io.batch, s0 + mc.chunk);
-        if (mc.kind == kKindSmall) {
+        if (KIND == kKindSmall) {
             // small-code path, regular rows only (keeps the kernel within its
             // register budget; the plan sends irregular codes to the generic path)
             char* smc = reinterpret_cast<char*>(smem);
@@ -48,6 +51,16 @@ mixed_kernel(const MixedArgs a) {
     }
 }
 
+template <int RULE>
+__global__ void __launch_bounds__(kMixedMaxWarps * 32, 2) mixed_small_kernel(const MixedArgs a) {
+    mixed_body<RULE, kKindSmall>(a);
+}
+
+template <int RULE>
+__global__ void __launch_bounds__(kMixedMaxWarps * 32) mixed_generic_kernel(const MixedArgs a) {
+    mixed_body<RULE, kKindGeneric>(a);
+}
+
 }  // namespace
 
 size_t mixed_warp_bytes(const DevBases& B, int kind) {
@@ -58,9 +71,14 @@ size_t mixed_warp_bytes(const DevBases& B, int kind) {
     return (size_t)generic_bp::warp_layout(B.DC, B.MP, B.mpad, B.n).per_warp;
 }
 
-cudaError_t launch_mixed(const MixedArgs& a, int warps, int rule, cudaStream_t s, int sm_count) {
-    const void* kern = rule == MBBP_RULE_NMS ? reinterpret_cast<const void*>(mixed_kernel<MBBP_RULE_NMS>)
-                                             : reinterpret_cast<const void*>(mixed_kernel<MBBP_RULE_SP>);
+cudaError_t launch_mixed(const MixedArgs& a, int kind, int warps, int rule, cudaStream_t s, int sm_count) {
+    const bool nms = rule == MBBP_RULE_NMS;
+    const void* kern =
+        kind == kKindSmall
+            ? (nms ? reinterpret_cast<const void*>(mixed_small_kernel<MBBP_RULE_NMS>)
+                   : reinterpret_cast<const void*>(mixed_small_kernel<MBBP_RULE_SP>))
+            : (nms ? reinterpret_cast<const void*>(mixed_generic_kernel<MBBP_RULE_NMS>)
+                   : reinterpret_cast<const void*>(mixed_generic_kernel<MBBP_RULE_SP>));
     const size_t smem = (size_t)warps * a.warp_bytes;
     int per_sm = 0;
     cudaError_t e = prepare_kernel(kern, warps * 32, smem, &per_sm);
@@ -69,10 +87,13 @@ cudaError_t launch_mixed(const MixedArgs& a, int warps, int rule, cudaStream_t s
     unsigned long long grid = (unsigned long long)per_sm * (unsigned long long)sm_count;
     if (want < grid) grid = want;
     if (grid == 0) return cudaSuccess;
-    if (rule == MBBP_RULE_NMS)
-        mixed_kernel<MBBP_RULE_NMS><<<(unsigned)grid, warps * 32, smem, s>>>(a);
-    else
-        mixed_kernel<MBBP_RULE_SP><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    if (kind == kKindSmall) {
+        if (nms) mixed_small_kernel<MBBP_RULE_NMS><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+        else mixed_small_kernel<MBBP_RULE_SP><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    } else {
+        if (nms) mixed_generic_kernel<MBBP_RULE_NMS><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+        else mixed_generic_kernel<MBBP_RULE_SP><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -928,7 +928,7 @@ void mbbp_plan_free(mbbp_plan* P) { delete P; }
 
 size_t mbbp_plan_workspace_size(const mbbp_plan* P, const int32_t* batches) {
     if (!P || !batches) return 0;
-    size_t total = 256;  // work counter
+    size_t total = 256;  // work counters
     for (size_t c = 0; c < P->codes.size(); ++c) {
         if (batches[c] < 0) return 0;
         total += align256((size_t)batches[c] * P->codes[c]->R * P->codes[c]->W * 4);
@@ -973,23 +973,31 @@ mbbp_status mixed_impl(const mbbp_plan* P, const mbbp_code_io* io, int iters, fl
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(MBBP_E_INVALID, "workspace must be 256-byte aligned");
     if (mbbp_status st = check_device(P->device)) return st;
-    MixedArgs a{};
+    // one launch per kernel body (small / generic), each with its own work
+    // list and counter; the launch holding the plan's first code goes first
+    MixedArgs args[2] = {};
     char* ws = static_cast<char*>(workspace);
     std::vector<uint32_t*> cand(nc);
     for (int c = 0; c < nc; ++c) {
         cand[c] = reinterpret_cast<uint32_t*>(ws);
         ws += align256((size_t)batches[c] * P->codes[c]->R * P->codes[c]->W * 4);
     }
-    a.counter = reinterpret_cast<unsigned long long*>(ws);
-    unsigned long long first = 0;
-    size_t warp_bytes = 16;
-    int slot = 0;
+    unsigned long long* counters = reinterpret_cast<unsigned long long*>(ws);
+    unsigned long long firsts[2] = {0, 0};
+    size_t wbytes[2] = {16, 16};
+    int slots[2] = {0, 0};
+    int launch_order[2] = {-1, -1};
     for (int oi = 0; oi < nc; ++oi) {
         const int c = P->order[oi];
         const mbbp_bases* B = P->codes[c];
         const mbbp_code_io& x = io[c];
         if (x.batch == 0) continue;
-        MixedCode& mc = a.codes[slot++];
+        const int k = P->kind[c];
+        if (launch_order[0] < 0) launch_order[0] = k;
+        else if (launch_order[0] != k) launch_order[1] = k;
+        MixedArgs& a = args[k];
+        unsigned long long& first = firsts[k];
+        MixedCode& mc = a.codes[slots[k]++];
         mc.B = B->dev;
         mc.kind = P->kind[c];
         mc.chunk = P->chunk[c];
@@ -1005,14 +1013,21 @@ mbbp_status mixed_impl(const mbbp_plan* P, const mbbp_code_io* io, int iters, fl
         mc.io.post = nullptr;
         mc.first = first;
         first += (unsigned long long)((x.batch + mc.chunk - 1) / mc.chunk) * B->R;
-        warp_bytes = std::max(warp_bytes, mixed_warp_bytes(B->dev, mc.kind));
+        wbytes[k] = std::max(wbytes[k], mixed_warp_bytes(B->dev, mc.kind));
     }
-    a.n_codes = slot;
-    a.total = first;
-    a.warp_bytes = (uint32_t)((warp_bytes + 15) & ~(size_t)15);
-    if ((size_t)P->warps * a.warp_bytes > 200 * 1024) return fail(MBBP_E_TOO_LARGE, "shared memory per block");
-    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess && a.total > 0) e = launch_mixed(a, P->warps, rule, s, P->sm_count);
+    for (int k = 0; k < 2; ++k) {
+        args[k].n_codes = slots[k];
+        args[k].total = firsts[k];
+        args[k].warp_bytes = (uint32_t)((wbytes[k] + 15) & ~(size_t)15);
+        args[k].counter = counters + k;
+        if ((size_t)P->warps * args[k].warp_bytes > 200 * 1024)
+            return fail(MBBP_E_TOO_LARGE, "shared memory per block");
+    }
+    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        const int k = launch_order[i];
+        if (k >= 0 && args[k].total > 0) e = launch_mixed(args[k], k, P->warps, rule, s, P->sm_count);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "mbbp_decode_mixed (BP)");
     for (int c = 0; c < nc; ++c) {
         const mbbp_code_io& x = io[c];

@@ -127,7 +127,7 @@ struct MixedArgs {
     unsigned long long* counter;
 };
 size_t mixed_warp_bytes(const DevBases& B, int kind);
-cudaError_t launch_mixed(const MixedArgs& a, int warps, int rule, cudaStream_t s, int sm_count);
+cudaError_t launch_mixed(const MixedArgs& a, int kind, int warps, int rule, cudaStream_t s, int sm_count);
 
 // Weighted min-sum forward / backward / decode (wms.cu).
 struct WmsArgs {
