@@ -157,6 +157,7 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
     // degrees, 4 bits per variable step; variable ids are re-read from L1
     // when a shot starts and ends
     uint4 desc[VS];
+    static_assert(VS <= 8 && RS <= 8, "degrees are packed 4 bits per step in 32 bits");
     uint32_t degs = 0;
 #pragma unroll
     for (int k = 0; k < VS; ++k) {
@@ -305,27 +306,6 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
             if (io.iters_run) io.iters_run[item] = (uint16_t)K_run;
         }
         __syncwarp();
-    }
-}
-
-// Dispatch on the small shape and row regularity of a representation set.
-template <int RULE>
-__device__ __forceinline__ void run_chunk_any(const DevBases& B, const ShotIO& io, int b, int s0,
-                                              int s1, char* smc, uint32_t wbase) {
-    const bool reg = B.regular != 0;
-    switch (B.shape) {
-        case 1:
-            if (reg) run_chunk<3, 2, 2, RULE, true>(B, io, b, s0, s1, smc, wbase);
-            else run_chunk<3, 2, 2, RULE, false>(B, io, b, s0, s1, smc, wbase);
-            break;
-        case 2:
-            if (reg) run_chunk<5, 3, 3, RULE, true>(B, io, b, s0, s1, smc, wbase);
-            else run_chunk<5, 3, 3, RULE, false>(B, io, b, s0, s1, smc, wbase);
-            break;
-        default:
-            if (reg) run_chunk<5, 4, 3, RULE, true>(B, io, b, s0, s1, smc, wbase);
-            else run_chunk<5, 4, 3, RULE, false>(B, io, b, s0, s1, smc, wbase);
-            break;
     }
 }
 

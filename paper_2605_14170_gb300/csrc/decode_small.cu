@@ -1,7 +1,7 @@
 // Single-code launch of the register-resident BP path for small codes (the
 // [[72,12,6]] and [[144,12,12]] bivariate bicycle codes of Section IV); the
-// per-chunk device code is in bp_small.cuh.  Warps pull (chunk of kChunk
-// shots, representation) work items from a global counter.
+// per-chunk device code is in bp_small.cuh.  Warps pull
+// (chunk of kChunk shots, representation) work items from a global counter.
 #include "bp_small.cuh"
 
 namespace mbbp {

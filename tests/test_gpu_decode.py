@@ -86,6 +86,18 @@ def test_bb144_nms_exact_r16(M, which):
     assert_exact(got, ref)
 
 
+@pytest.mark.parametrize("R,shots", [(16, 150), (32, 60)])
+def test_bb288_nms_exact(M, R, shots):
+    """[[288,12,18]] (the largest small-code shape: 9 variable steps, up to
+    224 rows of H^(t)), depolarizing p = 0.07, 100 iterations."""
+    c, H, e, s = workload("bb288", "HZ", shots, 0.07, "depolarizing")
+    B = M.mbbp_build_bases(H, R, SEED + 2)
+    llr = channel_llr(288, 2 * 0.07 / 3).astype(np.float32)
+    got = gpu_decode(M, B, s, llr, 100, 0.625)
+    ref = oracle.mbbp_decode(H, B.sets, s, llr, 100, 0.625, precision="f32")
+    assert_exact(got, ref)
+
+
 def test_per_shot_llrs_and_negative_llrs(M):
     """Per-shot LLR rows (llr_stride = n), including negative LLRs whose hard
     decision starts at 1, on the [[72,12,6]] code."""
