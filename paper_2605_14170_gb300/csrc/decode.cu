@@ -23,8 +23,14 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
-template <int DC, int DV, int RULE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// Block-size classes of the generic kernel: up to 8 warps (the usual case)
+// and up to 16 warps for big codes, where a block holds H's columns once plus
+// one message area per warp and one large block fits more warps per SM than
+// several small ones.  Each class is compiled for its own block size.
+constexpr int kGenericWideWarps = 16;
+
+template <int DC, int DV, int RULE, int MAXW>
+__global__ void __launch_bounds__(MAXW * 32)
 decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevBases& B = a.B;
@@ -212,18 +218,37 @@ cudaError_t launch_serial_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
 
 template <int K, int RULE>
 cudaError_t launch_decode_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
-    auto kern = decode_kernel<K, K, RULE>;
+    const void* narrow = reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock>);
+    const void* wide = reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps>);
     const generic_bp::WarpLayout L = generic_bp::warp_layout(K, a.B.MP, a.B.mpad, a.B.n);
-    int warps = kWarpsPerBlock;
-    while (warps > 1 && (size_t)L.hcol_bytes + (size_t)warps * L.per_warp > 200 * 1024) --warps;
+    // per class, the block size with the most resident warps per SM (ties:
+    // the smaller block) within 200 KB of shared memory per block; the wide
+    // class only when it holds at least a quarter more warps (its code,
+    // compiled for 512-thread blocks, takes more registers)
+    int choice[2][2] = {{0, 0}, {0, 0}};  // [class] = {warps per block, blocks per SM}
+    for (int w = 1; w <= kGenericWideWarps; ++w) {
+        const size_t sm_w = (size_t)L.hcol_bytes + (size_t)w * L.per_warp;
+        if (sm_w > 200 * 1024) break;
+        const int cls = w <= kWarpsPerBlock ? 0 : 1;
+        int b = 0;
+        cudaError_t e = prepare_kernel(cls == 0 ? narrow : wide, w * 32, sm_w, &b);
+        if (e != cudaSuccess) return e;
+        if (b * w > choice[cls][0] * choice[cls][1]) {
+            choice[cls][0] = w;
+            choice[cls][1] = b;
+        }
+    }
+    const bool use_wide = choice[1][0] > 0 && 4 * choice[1][0] * choice[1][1] >= 5 * choice[0][0] * choice[0][1];
+    const int warps = choice[use_wide][0], per_sm = choice[use_wide][1];
+    if (warps == 0) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)L.hcol_bytes + (size_t)warps * L.per_warp;
-    int per_sm = 0;
-    cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kern), warps * 32, smem, &per_sm);
-    if (e != cudaSuccess) return e;
     unsigned long long want = (a.total_items + warps - 1) / warps;
     unsigned long long grid = (unsigned long long)per_sm * (unsigned long long)sm_count;
     if (want < grid) grid = want;
-    kern<<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    if (use_wide)
+        decode_kernel<K, K, RULE, kGenericWideWarps><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    else
+        decode_kernel<K, K, RULE, kWarpsPerBlock><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -246,11 +271,6 @@ cudaError_t static_scratch(void** ptr) {
     }
     *ptr = g_scratch_addr[dev];
     return cudaSuccess;
-}
-
-size_t decode_smem_bytes(const DevBases& B, int warps) {
-    const generic_bp::WarpLayout L = generic_bp::warp_layout(B.DC, B.MP, B.mpad, B.n);
-    return (size_t)L.hcol_bytes + (size_t)warps * L.per_warp;
 }
 
 cudaError_t prepare_kernel(const void* func, int threads, size_t smem, int* blocks_per_sm) {

@@ -165,7 +165,6 @@ cudaError_t launch_decode_serial(const DecodeArgs& a, cudaStream_t s, int sm_cou
 cudaError_t launch_decode_serial_generic(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_decode_small(const DecodeArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_fws(const FwsArgs& a, cudaStream_t s);
-size_t decode_smem_bytes(const DevBases& B, int warps);
 // Device address of the fixed scratch array on the current device (looked up
 // on the first call per device).
 cudaError_t static_scratch(void** ptr);
