@@ -40,7 +40,7 @@ def train_wms(B: "mbbp.Bases", p: float, T: int = 25, ckpt: int = 5, batch: int 
               lr: float = 1e-3, seed: int = 20260516, alpha: float = 0.625, which: str = "X",
               w_bounds=(0.0, 2.0), g_bounds=(0.0, 0.9), all_iters: bool = True, log_every: int = 10,
               L: "mbbp.Logicals | None" = None, val_shots: int = 20000, val_every: int = 25,
-              val_iters: int = 100, device="cuda"):
+              val_iters: int = 100, val_p: float | None = None, device="cuda"):
     """Train per-edge, per-iteration weights w and damping g of WMS on the
     representations B (built from H_Z for X errors, H_X for Z errors).
     The loss is the BCE of every iteration's posterior (all_iters, which
@@ -48,7 +48,9 @@ def train_wms(B: "mbbp.Bases", p: float, T: int = 25, ckpt: int = 5, batch: int 
     With logical operators L, the weights are scored every `val_every` steps
     by their logical failures on `val_shots` held-out shots (decoded with the
     halting rule, up to `val_iters` iterations) and the best weights seen are
-    returned, the initial (plain min-sum) weights included.
+    returned, the initial (plain min-sum) weights included.  The held-out
+    shots are drawn at `val_p` (default: p), e.g. a higher error rate where
+    a strong code still fails often enough to tell weights apart.
     Returns (w, g, history) with history = [(step, mean BCE, validation
     failures or None)]."""
     import torch
@@ -70,11 +72,13 @@ def train_wms(B: "mbbp.Bases", p: float, T: int = 25, ckpt: int = 5, batch: int 
     if L is not None:
         vx = torch.empty((val_shots, W), dtype=torch.int32, device=device)
         vz = torch.empty_like(vx)
-        mbbp.mbbp_sample_errors(n, val_shots, 5_000_000_000, seed + 1, p, mbbp.NOISE_DEPOLARIZING, vx, vz)
+        vp = p if val_p is None else val_p
+        vllr = _llr(n, vp, device)
+        mbbp.mbbp_sample_errors(n, val_shots, 5_000_000_000, seed + 1, vp, mbbp.NOISE_DEPOLARIZING, vx, vz)
         ve = vx if which == "X" else vz
         vsyn = torch.empty((val_shots, B.m), dtype=torch.uint8, device=device)
         mbbp.mbbp_syndrome(B, ve, vsyn)
-        f0 = _failures(B, L, w, g, vsyn, ve, llr, val_iters, device)
+        f0 = _failures(B, L, w, g, vsyn, ve, vllr, val_iters, device)
         best = (f0, 0, w.clone(), g.clone())
         history.append((0, None, f0))
     for k in range(steps):
@@ -89,7 +93,7 @@ def train_wms(B: "mbbp.Bases", p: float, T: int = 25, ckpt: int = 5, batch: int 
         mbbp.mbbp_adam_step(g, gg, mg, vg, lr, 0.9, 0.999, 1e-8, k + 1, *g_bounds)
         val = None
         if L is not None and ((k + 1) % val_every == 0 or k == steps - 1):
-            val = _failures(B, L, w, g, vsyn, ve, llr, val_iters, device)
+            val = _failures(B, L, w, g, vsyn, ve, vllr, val_iters, device)
             if val < best[0]:
                 best = (val, k + 1, w.clone(), g.clone())
         if val is not None or (log_every and (k % log_every == 0 or k == steps - 1)):
