@@ -26,7 +26,8 @@ namespace mbbp {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWmsWarps = 4;
+constexpr int kWmsWarps = 8;       // largest block (warps); the launch picks the block size
+constexpr int kWmsStateWarps = 4;  // warps whose segment states must fit for the shared-memory path
 
 struct WmsLayout {
     int S, npad, ehpad;
@@ -442,18 +443,26 @@ cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm
     // backward: keep the segment states in shared memory when four warps'
     // worth fits in about half of an SM's shared memory
     const size_t st_bytes = (size_t)a.ckpt * L.S * 4;
-    const bool smem_st = backward && (size_t)kWmsWarps * (L.bwd_bytes + st_bytes) <= 110 * 1024;
+    const bool smem_st = backward && (size_t)kWmsStateWarps * (L.bwd_bytes + st_bytes) <= 110 * 1024;
     const size_t per_warp = backward ? L.bwd_bytes + (smem_st ? st_bytes : 0) : L.fwd_bytes;
-    int warps = kWmsWarps;
-    while (warps > 1 && warps * per_warp > 200 * 1024) --warps;
     if (per_warp > 200 * 1024) return cudaErrorInvalidConfiguration;
-    const size_t smem = warps * per_warp;
     const void* kern = !backward ? reinterpret_cast<const void*>(wms_forward_kernel<K, K>)
                        : smem_st ? reinterpret_cast<const void*>(wms_backward_kernel<K, K, true>)
                                  : reinterpret_cast<const void*>(wms_backward_kernel<K, K, false>);
-    int per_sm = 0;
-    cudaError_t e = prepare_kernel(kern, warps * 32, smem, &per_sm);
-    if (e != cudaSuccess) return e;
+    // the block size with the most resident warps per SM (ties: the smaller
+    // block), within 200 KB of shared memory per block
+    int warps = 0, per_sm = 0;
+    for (int w = 1; w <= kWmsWarps && (size_t)w * per_warp <= 200 * 1024; ++w) {
+        int b = 0;
+        cudaError_t e = prepare_kernel(kern, w * 32, (size_t)w * per_warp, &b);
+        if (e != cudaSuccess) return e;
+        if (b * w > per_sm * warps) {
+            warps = w;
+            per_sm = b;
+        }
+    }
+    if (warps == 0) return cudaErrorInvalidConfiguration;
+    const size_t smem = warps * per_warp;
     unsigned long long want = (a.total_items + warps - 1) / warps;
     unsigned long long grid = (unsigned long long)per_sm * sm_count;
     if (want < grid) grid = want;
