@@ -8,7 +8,7 @@ namespace mbbp {
 namespace {
 
 constexpr int kSmallWarps = 8;
-constexpr int kChunk = 4;  // shots per work item of a warp (same representation)
+constexpr int kChunk = 8;  // shots per work item of a warp (same representation)
 
 // Blocks per SM the register budget is sized for (measured: 3 blocks at 80
 // registers issue more instructions than they gain in occupancy).
