@@ -41,8 +41,8 @@ ALPHA = 0.625
 SEED = 20260515
 OPS_PER_EDGE_UPDATE = 10  # algorithmic ALU operations per edge-update (min-sum flooding)
 # DRAM bytes per shot of the BP kernel (ncu capture of a 100k-shot launch:
-# 7.33 MB read + 2.6 KB written); None once the kernel changes
-DRAM_BYTES_PER_SHOT = (7.33e6 + 2.6e3) / 100000
+# 7.31 MB read + 2.6 KB written); None once the kernel changes
+DRAM_BYTES_PER_SHOT = (7.311e6 + 2.56e3) / 100000
 WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
 
 
