@@ -10,9 +10,12 @@ namespace mbbp {
 namespace {
 
 constexpr int kSerialWarps = 8;
+// Blocks per SM the register budget is sized for (80 registers; measured
+// against 2 blocks at 119 registers and 4 at 64: 2-4% and 10-12% slower).
+constexpr int kSerialMinBlocks = 3;
 
 template <int DC, int NO, int NV, int RULE, bool REG, int CS>
-__global__ void __launch_bounds__(kSerialWarps * 32, 2)
+__global__ void __launch_bounds__(kSerialWarps * 32, kSerialMinBlocks)
 decode_serial_chunk_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevBases& B = a.B;
