@@ -299,7 +299,7 @@ mbbp_status mbbp_decode_mixed(const mbbp_plan* P, const mbbp_code_io* io, int it
                               int rule, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Choose the plan's launch configuration by timing mbbp_decode_mixed on the
- * given inputs (coordinate descent over warps per block in {4, 8}, shots per
+ * given inputs (coordinate descent over warps per block in {4, 6, 7, 8}, shots per
  * work item in {1, 2, 4, 8, 16} and the kernel path per code, then the code
  * order).  Synchronises the stream, overwrites the outputs; not capturable.
  * best_ms: host float or NULL, the time of the chosen configuration. */

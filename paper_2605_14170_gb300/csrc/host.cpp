@@ -1096,7 +1096,7 @@ mbbp_status mbbp_plan_autotune(mbbp_plan* P, const mbbp_code_io* io, int iters, 
         else *knob = old;
         return MBBP_OK;
     };
-    for (int w : {4, 8}) if (st == MBBP_OK) st = try_value(&P->warps, w);
+    for (int w : {4, 6, 7, 8}) if (st == MBBP_OK) st = try_value(&P->warps, w);
     for (int c = 0; c < nc && st == MBBP_OK; ++c) {
         for (int ch : {1, 2, 4, 8, 16}) if (st == MBBP_OK) st = try_value(&P->chunk[c], ch);
         if (st == MBBP_OK && P->codes[c]->dev.shape != 0 && P->codes[c]->regular)
