@@ -1,10 +1,11 @@
 // Device code of the serial-schedule path for kernel widths 6 and 8.
 //
 // A warp decodes shots of one representation, CS at a time, pulling them
-// from a per-representation counter.  Each shot
-// keeps its check-to-variable messages m_{c->v} in shared memory (edge j of
-// row r at slot j * MP + r, followed by one slot holding -0.0f, the exact
-// additive identity of IEEE addition).  A serial iteration visits the layers
+// from a per-representation counter.  Each shot keeps its check-to-variable
+// messages m_{c->v} in shared memory (edge j of the row at position p at
+// slot j * MP + p, followed by one slot holding -0.0f, the exact additive
+// identity of IEEE addition); the host places the rows (a permutation of
+// the positions) so that the lanes of one access hit different banks.  A serial iteration visits the layers
 // of the representation in order; within a layer the (row, shot) pairs are
 // spread over the lanes.  Rows of a layer share no variable, so the pairs of
 // one layer read only messages of other layers' rows and write only their
@@ -26,24 +27,6 @@ namespace mbbp {
 namespace serial_bp {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-struct Layout {
-    int SH;     // floats per shot message area (DC * MP messages, the -0 slot, padding)
-    int NP;     // floats of mu per shot
-    int EP;     // bytes of hard decisions per shot (n + 1 rounded to 16)
-    int RW;     // syndrome words per shot (MP / 32)
-    int bytes;  // per warp (a multiple of 16)
-};
-
-__host__ __device__ __forceinline__ Layout layout(int DC, int MP, int n, int CS) {
-    Layout L;
-    L.SH = DC * MP + 4;
-    L.NP = (n + 3) & ~3;
-    L.EP = (n + 16) & ~15;
-    L.RW = MP >> 5;
-    L.bytes = CS * (L.SH * 4 + L.NP * 4 + L.EP) + ((CS * L.RW * 4 + 15) & ~15);
-    return L;
-}
 
 __device__ __forceinline__ float lds_b(const float* base, uint32_t byte_off) {
     return *reinterpret_cast<const float*>(reinterpret_cast<const char*>(base) + byte_off);
@@ -73,7 +56,8 @@ __device__ __forceinline__ float var_post(const float* msg, float mu, uint4 d) {
 }
 
 // Load shot `shot` into slot sh: zero messages, the -0.0f slot, LLRs, the
-// hard decision of the LLRs and the syndrome bits of the rows of H^(t).
+// hard decision of the LLRs and the syndrome bits of the rows of H^(t) (by
+// row position) and of the rows of H (by row).
 template <int DC, int CS>
 __device__ __forceinline__ void load_shot(const DevBases& B, const ShotIO& io, int b, int shot, int sh,
                                           const Layout& L, float* msg, float* mu, uint8_t* eh,
@@ -81,7 +65,7 @@ __device__ __forceinline__ void load_shot(const DevBases& B, const ShotIO& io, i
     const int lane = threadIdx.x & 31;
     const int MP = B.MP, n = B.n, m = B.m;
     const int Mb = __ldg(B.rows + b);
-    const uint32_t* rinfo = B.rowinfo + (size_t)b * MP;
+    const uint32_t* rinfo = B.rinfo_s + (size_t)b * MP;
     const unsigned long long item = (unsigned long long)shot * B.R + b;
     const float* llr = io.llr + (size_t)shot * io.llr_stride;
     const uint8_t* sy = io.synd + (size_t)shot * m;
@@ -96,11 +80,18 @@ __device__ __forceinline__ void load_shot(const DevBases& B, const ShotIO& io, i
         if (io.post) io.post[item * n + v] = x;
     }
     if (lane == 0) eh[sh * L.EP + n] = 0;  // padding column of hcol
+    // syndrome bits by row position (check rule) and by row of H (halting)
+    uint32_t* sbh = sbits + CS * L.RW;
     for (int k = 0; k < L.RW; ++k) {
         const int r = lane + 32 * k;
         const uint32_t bit = (r < Mb) ? (uint32_t)(__ldg(sy + (__ldg(rinfo + r) & 0xffffu)) & 1u) : 0u;
         const uint32_t word = __ballot_sync(kFull, bit);
-        if (lane == 0) sbits[sh * L.RW + k] = word;
+        const uint32_t hbit = (r < m) ? (uint32_t)(__ldg(sy + r) & 1u) : 0u;
+        const uint32_t hword = __ballot_sync(kFull, hbit);
+        if (lane == 0) {
+            sbits[sh * L.RW + k] = word;
+            sbh[sh * L.RW + k] = hword;
+        }
     }
     __syncwarp();
 }
@@ -148,8 +139,8 @@ __device__ __forceinline__ void run_rep(const DevBases& B, const ShotIO& io, int
     uint8_t* eh = reinterpret_cast<uint8_t*>(mu + CS * L.NP);
     uint32_t* sbits = reinterpret_cast<uint32_t*>(eh + CS * L.EP);
     const int nl = __ldg(B.nlayers + b);
-    const uint32_t* rinfo = B.rowinfo + (size_t)b * MP;
-    const uint16_t* lrows = B.lrows + (size_t)b * MP;
+    const uint32_t* rinfo = B.rinfo_s + (size_t)b * MP;
+    const uint16_t* lrows = B.lpos + (size_t)b * MP;
     const uint16_t* lptr = B.lptr + (size_t)b * (MP + 1);
     const uint4* ed = B.edesc + (size_t)b * DC * MP;
     const uint4* vd = B.vdesc3 + (size_t)b * n;
@@ -171,7 +162,7 @@ __device__ __forceinline__ void run_rep(const DevBases& B, const ShotIO& io, int
 #pragma unroll
         for (int sh = 0; sh < CS; ++sh) {
             while ((active >> sh) & 1u) {
-                const bool ok = halted<DC>(m, mpad, hcol, eh + sh * L.EP, sbits + sh * L.RW);
+                const bool ok = halted<DC>(m, mpad, hcol, eh + sh * L.EP, sbits + CS * L.RW + sh * L.RW);
                 if (!ok && iter[sh] < io.iters) break;
                 const unsigned long long item = (unsigned long long)shot[sh] * R + b;
                 generic_bp::store_item(io, item, n, W, eh + sh * L.EP, ok, iter[sh]);

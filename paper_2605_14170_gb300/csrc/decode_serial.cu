@@ -9,7 +9,7 @@
 namespace mbbp {
 namespace {
 
-constexpr int kSerialWarps = 8;
+constexpr int kSerialWarps = serial_bp::kWarps;
 // Blocks per SM the register budget is sized for (80 registers; measured
 // against 2 blocks at 119 registers and 4 at 64: 2-4% and 10-12% slower).
 constexpr int kSerialMinBlocks = 3;
@@ -59,12 +59,11 @@ cudaError_t launch_cs(const DecodeArgs& a, cudaStream_t s, int sm_count) {
     // descriptors of the blocks' representations), else the largest warp
     // count at CS = 1 that fits once
     const size_t hb = (size_t)generic_bp::align16(DC * a.B.mpad * 2);
-    const size_t budget2 = 56 * 1024, budget1 = 200 * 1024;
-    if (hb + kSerialWarps * (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 4).bytes <= budget2)
-        return launch_t<DC, NO, NV, RULE, REG, 4>(a, s, sm_count, kSerialWarps);
-    if (hb + kSerialWarps * (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 2).bytes <= budget2)
-        return launch_t<DC, NO, NV, RULE, REG, 2>(a, s, sm_count, kSerialWarps);
-    if (hb + kSerialWarps * (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 1).bytes <= budget2)
+    const size_t budget1 = 200 * 1024;
+    const int cs = serial_bp::shots_per_warp(DC, a.B.MP, a.B.mpad, a.B.n);
+    if (cs == 4) return launch_t<DC, NO, NV, RULE, REG, 4>(a, s, sm_count, kSerialWarps);
+    if (cs == 2) return launch_t<DC, NO, NV, RULE, REG, 2>(a, s, sm_count, kSerialWarps);
+    if (hb + kSerialWarps * (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 1).bytes <= serial_bp::kBudget2)
         return launch_t<DC, NO, NV, RULE, REG, 1>(a, s, sm_count, kSerialWarps);
     int warps = kSerialWarps;
     const size_t per = (size_t)serial_bp::layout(DC, a.B.MP, a.B.n, 1).bytes;

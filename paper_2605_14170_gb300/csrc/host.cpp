@@ -299,6 +299,99 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, ui
     return L;
 }
 
+// Row positions for the serial chunk kernel.  In a layer the kernel spreads
+// (row, shot) pairs over the lanes, 32 / CS rows per lane step; for edge j of
+// its row a lane stores to slot j * MP + pos(row) and gathers the messages of
+// the edge's variable from the slots j' * MP + pos(row') of its other rows.
+// With MP a multiple of 32, slot s of shot sh sits in bank
+// (pos + 4 sh) mod 32, so the accesses of one instruction conflict when the
+// positions they touch collide mod 32.  Simulated annealing over a
+// permutation of the positions 0..M-1 minimizes the summed worst bank load
+// of every (layer, lane step, j, access) group; the arithmetic is unchanged
+// (the gathers keep ascending row order), only bank conflicts change.
+std::vector<int> serial_positions(const std::vector<std::vector<int>>& rcols, const std::vector<int>& layer_of,
+                                  const std::vector<int>& idx_in_layer, int CS, int DC, int n, uint64_t seed) {
+    const int M = (int)rcols.size();
+    std::vector<int> pos(M);
+    for (int r = 0; r < M; ++r) pos[r] = r;
+    if (M < 2) return pos;
+    std::vector<std::vector<int>> vrows(n);  // rows of each variable, ascending
+    for (int r = 0; r < M; ++r)
+        for (int v : rcols[r]) vrows[v].push_back(r);
+    int maxdv = 1;
+    for (int v = 0; v < n; ++v) maxdv = std::max(maxdv, (int)vrows[v].size());
+    const int A = maxdv;  // accesses per edge: the store and up to maxdv - 1 gathers
+    const int rpg = std::max(1, 32 / CS);
+    // cell of (layer, lane step, j, access)
+    int nl = 0, maxg = 0;
+    for (int r = 0; r < M; ++r) {
+        nl = std::max(nl, layer_of[r] + 1);
+        maxg = std::max(maxg, idx_in_layer[r] / rpg + 1);
+    }
+    auto cell = [&](int L, int gidx, int j, int a) { return ((L * maxg + gidx) * DC + j) * A + a; };
+    const int ncell = nl * maxg * DC * A;
+    std::vector<std::vector<int>> target_cells(M);  // cells each row's position appears in
+    for (int r = 0; r < M; ++r) {
+        const int L = layer_of[r], gidx = idx_in_layer[r] / rpg;
+        for (int j = 0; j < (int)rcols[r].size() && j < DC; ++j) {
+            target_cells[r].push_back(cell(L, gidx, j, 0));
+            int a = 1;
+            for (int r2 : vrows[rcols[r][j]])
+                if (r2 != r && a < A) target_cells[r2].push_back(cell(L, gidx, j, a++));
+        }
+    }
+    std::vector<int> cnt((size_t)ncell * 32, 0), mx(ncell, 0);
+    auto add = [&](int r, int d) {
+        for (int c : target_cells[r])
+            for (int sh = 0; sh < CS; ++sh) cnt[(size_t)c * 32 + ((pos[r] + 4 * sh) & 31)] += d;
+    };
+    auto remax = [&](int c) {
+        int x = 0;
+        for (int k = 0; k < 32; ++k) x = std::max(x, cnt[(size_t)c * 32 + k]);
+        mx[c] = x;
+    };
+    for (int r = 0; r < M; ++r) add(r, 1);
+    for (int c = 0; c < ncell; ++c) remax(c);
+    uint64_t rs = seed;
+    auto rnd = [&]() {
+        rs += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = rs;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    };
+    std::vector<int> cells;
+    const int iters = 12000;
+    for (int it = 0; it < iters; ++it) {
+        const double T = 0.6 * (1.0 - (double)it / iters) + 0.02;
+        const int a = (int)(rnd() % M), b = (int)(rnd() % M);
+        if (a == b || ((pos[a] ^ pos[b]) & 31) == 0) continue;
+        cells.clear();
+        for (int r : {a, b}) cells.insert(cells.end(), target_cells[r].begin(), target_cells[r].end());
+        std::sort(cells.begin(), cells.end());
+        cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
+        long before = 0, after = 0;
+        for (int c : cells) before += mx[c];
+        add(a, -1);
+        add(b, -1);
+        std::swap(pos[a], pos[b]);
+        add(a, 1);
+        add(b, 1);
+        for (int c : cells) { remax(c); after += mx[c]; }
+        const long d = after - before;
+        const double u = (double)(rnd() >> 11) * (1.0 / 9007199254740992.0);
+        if (!(d <= 0 || u < std::exp(-(double)d / T))) {
+            add(a, -1);
+            add(b, -1);
+            std::swap(pos[a], pos[b]);
+            add(a, 1);
+            add(b, 1);
+            for (int c : cells) remax(c);
+        }
+    }
+    return pos;
+}
+
 mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set_ptr,
                        const int32_t* set_rows, mbbp_bases** out) {
     if (!out) return fail(MBBP_E_INVALID, "out is NULL");
@@ -360,6 +453,8 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     const uint32_t negz = 4u * (uint32_t)(K * MP);
     std::vector<uint4> edesc(chunked ? (size_t)R * K * MP : 0, make_uint4(0, 0, 0, 0));
     std::vector<uint4> vdesc3(chunked ? (size_t)R * n : 0, make_uint4(0, 0, 0, 0));
+    std::vector<uint16_t> lpos(chunked ? (size_t)R * MP : 0, 0);
+    std::vector<uint32_t> rinfo_s(chunked ? (size_t)R * MP : 0, 0);
     B->lorder.assign((size_t)R * MP, 0);
     B->lptr.assign((size_t)R * (MP + 1), 0);
     B->nlayers.assign(R, 0);
@@ -382,27 +477,6 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         for (int v = 0; v < n; ++v) ord[v] = v;
         std::stable_sort(ord.begin(), ord.end(),
                          [&](int a, int b) { return vl[a].size() < vl[b].size(); });
-        if (chunked) {
-            auto pack = [](const uint32_t* o) {
-                return make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
-                                  o[6] | (o[7] << 16));
-            };
-            for (int v = 0; v < n; ++v) {
-                uint32_t o[8];
-                for (int i = 0; i < 8; ++i) o[i] = i < (int)vl[v].size() ? 4u * vl[v][i] : negz;
-                vdesc3[(size_t)t * n + v] = pack(o);
-                for (int k = 0; k < (int)vl[v].size(); ++k) {
-                    const uint32_t slot = vl[v][k];
-                    uint32_t e[8];
-                    e[0] = (uint32_t)v;
-                    int c = 1;
-                    for (int i = 0; i < (int)vl[v].size(); ++i)
-                        if (i != k) e[c++] = 4u * vl[v][i];
-                    while (c < 8) e[c++] = negz;
-                    edesc[(size_t)t * K * MP + slot] = pack(e);
-                }
-            }
-        }
         std::vector<uint2> vstart(n);
         for (int p = 0; p < n; ++p) {
             const int v = ord[p];
@@ -443,6 +517,44 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         }
         lp[nl] = pos;
         B->nlayers[t] = nl;
+        if (chunked) {
+            // chunk kernel: rows at bank-aware positions, descriptors by position
+            std::vector<std::vector<int>> rc(M);
+            std::vector<int> idx_in(M);
+            for (int r = 0; r < M; ++r) {
+                const int src = r < m ? r : set_rows[set_ptr[t] + (r - m)];
+                rc[r] = g.rcols[src];
+            }
+            for (int L = 0; L < nl; ++L)
+                for (int i = lp[L]; i < lp[L + 1]; ++i) idx_in[lo[i]] = i - lp[L];
+            const int CS = serial_bp::shots_per_warp(K, MP, mpad, n);
+            const std::vector<int> sp = serial_positions(rc, layer_of, idx_in, CS, K, n, 0xBA4Cull + (uint64_t)t);
+            for (int i = 0; i < M; ++i) lpos[(size_t)t * MP + i] = (uint16_t)sp[lo[i]];
+            for (int r = 0; r < M; ++r) {
+                const int src = r < m ? r : set_rows[set_ptr[t] + (r - m)];
+                rinfo_s[(size_t)t * MP + sp[r]] = (uint32_t)src | ((uint32_t)rc[r].size() << 16);
+            }
+            auto pack = [](const uint32_t* o) {
+                return make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
+                                  o[6] | (o[7] << 16));
+            };
+            // slot j * MP + r of the logical layout -> byte offset of j * MP + pos(r)
+            auto off = [&](uint32_t slot) { return 4u * (uint32_t)((slot / MP) * MP + sp[slot % MP]); };
+            for (int v = 0; v < n; ++v) {
+                uint32_t o[8];
+                for (int i = 0; i < 8; ++i) o[i] = i < (int)vl[v].size() ? off(vl[v][i]) : negz;
+                vdesc3[(size_t)t * n + v] = pack(o);
+                for (int k = 0; k < (int)vl[v].size(); ++k) {
+                    uint32_t e[8];
+                    e[0] = (uint32_t)v;
+                    int c = 1;
+                    for (int i = 0; i < (int)vl[v].size(); ++i)
+                        if (i != k) e[c++] = off(vl[v][i]);
+                    while (c < 8) e[c++] = negz;
+                    edesc[(size_t)t * K * MP + off(vl[v][k]) / 4] = pack(e);
+                }
+            }
+        }
     }
     std::vector<uint16_t> lrows16(B->lorder.begin(), B->lorder.end());
     std::vector<uint16_t> lptr16(B->lptr.begin(), B->lptr.end());
@@ -532,7 +644,9 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     const size_t o_evar = o_nlayers + align256((size_t)R * 4);
     const size_t o_edesc = o_evar + align256(evar.size() * sizeof(uint2));
     const size_t o_vdesc3 = o_edesc + align256(edesc.size() * sizeof(uint4));
-    const size_t total = o_vdesc3 + align256(vdesc3.size() * sizeof(uint4));
+    const size_t o_lpos = o_vdesc3 + align256(vdesc3.size() * sizeof(uint4));
+    const size_t o_rinfo_s = o_lpos + align256(lpos.size() * 2);
+    const size_t total = o_rinfo_s + align256(rinfo_s.size() * 4);
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
     if (e == cudaSuccess) e = cudaMalloc(&B->dmem, total);
@@ -558,6 +672,8 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         {o_evar, evar.data(), evar.size() * sizeof(uint2)},
         {o_edesc, edesc.data(), edesc.size() * sizeof(uint4)},
         {o_vdesc3, vdesc3.data(), vdesc3.size() * sizeof(uint4)},
+        {o_lpos, lpos.data(), lpos.size() * 2},
+        {o_rinfo_s, rinfo_s.data(), rinfo_s.size() * 4},
     };
     for (const Copy& c : copies) {
         if (c.bytes == 0) continue;
@@ -591,6 +707,8 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     d.evar = reinterpret_cast<const uint2*>(base + o_evar);
     d.edesc = chunked ? reinterpret_cast<const uint4*>(base + o_edesc) : nullptr;
     d.vdesc3 = chunked ? reinterpret_cast<const uint4*>(base + o_vdesc3) : nullptr;
+    d.lpos = chunked ? reinterpret_cast<const uint16_t*>(base + o_lpos) : nullptr;
+    d.rinfo_s = chunked ? reinterpret_cast<const uint32_t*>(base + o_rinfo_s) : nullptr;
     *out = B;
     return MBBP_OK;
 }

@@ -54,9 +54,48 @@ struct DevBases {
     // the variable (byte offsets of their slots, ascending row, padded with
     // the offset 4 * DC * MP of a -0.0f slot); per variable, its 8 slot byte
     // offsets (ascending row, padded the same way).
-    const uint4* edesc;       // [R][DC*MP]
+    const uint4* edesc;       // [R][DC*MP], by row position
     const uint4* vdesc3;      // [R][n]
+    // chunk-kernel row positions (a permutation of the rows of H^(t) placed
+    // to spread the kernel's shared-memory accesses over the banks): the
+    // positions in layer order, and per position src row | degree << 16
+    const uint16_t* lpos;     // [R][MP]
+    const uint32_t* rinfo_s;  // [R][MP]
 };
+
+// Shared memory of one warp of the serial chunk kernel (bp_serial.cuh) for
+// CS shots, and the CS the launch uses (the host places rows for it).
+namespace serial_bp {
+struct Layout {
+    int SH;     // floats per shot message area (DC * MP messages, the -0 slot, padding)
+    int NP;     // floats of mu per shot
+    int EP;     // bytes of hard decisions per shot (n + 1 rounded to 16)
+    int RW;     // syndrome words per shot (MP / 32), twice: by row position, by row of H
+    int bytes;  // per warp (a multiple of 16)
+};
+
+__host__ __device__ inline Layout layout(int DC, int MP, int n, int CS) {
+    Layout L;
+    L.SH = DC * MP + 4;
+    L.NP = (n + 3) & ~3;
+    L.EP = (n + 16) & ~15;
+    L.RW = MP >> 5;
+    L.bytes = CS * (L.SH * 4 + L.NP * 4 + L.EP) + ((2 * CS * L.RW * 4 + 15) & ~15);
+    return L;
+}
+
+constexpr int kWarps = 8;              // warps per block
+constexpr int kBudget2 = 56 * 1024;    // shared memory per block that leaves about half of an SM to L1
+
+// The largest CS in {4, 2, 1} whose 8-warp block fits kBudget2 (1 when none
+// does; the launch then takes fewer warps at CS = 1).
+inline int shots_per_warp(int DC, int MP, int mpad, int n) {
+    const int hb = (DC * mpad * 2 + 15) & ~15;
+    for (int cs : {4, 2})
+        if (hb + kWarps * layout(DC, MP, n, cs).bytes <= kBudget2) return cs;
+    return 1;
+}
+}  // namespace serial_bp
 
 // Bank rotation of edge position j in the small-code layout.
 __host__ __device__ constexpr int slot_rot(int j) { return (j * 11) & 31; }
