@@ -102,7 +102,7 @@ def test_serial_edge_cases_exact(M):
 
 def test_serial_irregular_and_wide(M):
     """Per-row degrees in the width-8 kernel, and the length-882 GB code
-    (width 8) with R = 16."""
+    (width 6, the generic-size rows of H^(t)) with R = 16."""
     rng = np.random.default_rng(7)
     m, n = 40, 90
     H = np.zeros((m, n), np.uint8)
@@ -193,3 +193,26 @@ def test_decode_ex_defaults_and_errors(M):
                 M.Options(0, 0.0, 1, 1)):
         with pytest.raises(M.MBBPError):
             M.mbbp_decode_ex(B, st, lt, 50, bad, out["e_hat"], out["conv"], out["success"], ws)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_width12_code_both_schedules(M, rule):
+    """Rows of weight up to 11: the width-12 kernels (generic flooding kernel
+    and the one-item-per-warp serial kernel), min-sum exact, sum-product by
+    agreement."""
+    rng = np.random.default_rng(12)
+    m, n = 30, 120
+    H = np.zeros((m, n), np.uint8)
+    for r in range(m):
+        H[r, rng.choice(n, int(rng.integers(5, 12)), replace=False)] = 1
+    e = (rng.random((120, n)) < 0.03).astype(np.uint8)
+    s = oracle.syndrome(H, e)
+    B = M.mbbp_build_bases_from_sets(H, oracle.collect_subtrees(H, 4, 5))
+    llr = channel_llr(n, 0.03).astype(np.float32)
+    for schedule in (0, SERIAL):
+        got = gpu(M, B, s, llr, 30, 0.8, rule, schedule=schedule)
+        r = ref(H, B, s, llr, 30, 0.8, rule, schedule=schedule)
+        if rule == 0:
+            assert_exact(got, r)
+        else:
+            assert (got["e_hat"] == r["ehat"]).all(1).mean() >= 0.97
