@@ -41,9 +41,10 @@ __host__ __device__ inline WmsLayout wms_layout(int DC, int MP, int n, int ckpt)
     L.ehpad = (n + 1 + 15) & ~15;
     // forward: m, q (S each), mu, post (npad each), hard decision bytes
     L.fwd_bytes = (size_t)(2 * L.S + 2 * L.npad) * 4 + L.ehpad;
-    // backward: q, gm, gm_prev, gq (S each), mu (npad); the segment's states
+    // backward: q, gm (updated in place from dL/dm^(t) to dL/dm^(t-1)), gq
+    // (S each), mu (npad); the segment's states follow in shared memory or
     // live in a per-warp global buffer of ckpt * S floats
-    L.bwd_bytes = (size_t)(4 * L.S + L.npad) * 4;
+    L.bwd_bytes = (size_t)(3 * L.S + L.npad) * 4;
     return L;
 }
 
@@ -252,8 +253,7 @@ wms_backward_kernel(const WmsArgs a) {
                             : a.seg_buf + gwarp * (size_t)a.ckpt * L.S;  // [ckpt][S], this warp's
     float* q = reinterpret_cast<float*>(wbase);
     float* gm = q + L.S;
-    float* gmp = gm + L.S;
-    float* gq = gmp + L.S;
+    float* gq = gm + L.S;
     float* mu = gq + L.S;
     for (;;) {
         unsigned long long item = 0;
@@ -378,7 +378,7 @@ wms_backward_kernel(const WmsArgs a) {
                         const float c = ww * sgn * mn;
                         atomicAdd(ggt + e0 + j, gmj * (mprev[j * MP + r] - c));
                         atomicAdd(gwt + e0 + j, gmj * (1.0f - gg) * sgn * mn);
-                        gmp[j * MP + r] = gmj * gg;
+                        gm[j * MP + r] = gmj * gg;  // becomes dL/dm^(t-1): only this lane owns the slot
                         const float gmn = gmj * (1.0f - gg) * ww * sgn;
                         if (own) G2 += gmn;
                         else G1 += gmn;
@@ -411,12 +411,10 @@ wms_backward_kernel(const WmsArgs a) {
                         }
                         for (int i = 0; i < deg; ++i) {
                             const int e = __ldg(sl + i);
-                            gmp[e] += G - gq[e] + gp;
+                            gm[e] += G - gq[e] + gp;
                         }
                     }
                 }
-                __syncwarp();
-                for (int i = lane; i < L.S; i += 32) gm[i] = gmp[i];
                 __syncwarp();
             }
         }
