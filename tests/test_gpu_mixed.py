@@ -77,7 +77,7 @@ def test_autotune_keeps_results_and_graph_replay():
     best = mbbp.mbbp_plan_autotune(P, ios, 100, 0.625, mbbp.RULE_NMS, ws)
     assert best > 0
     info = mbbp.mbbp_plan_info(P)
-    assert info["warps"] in (4, 8) and all(c in (1, 2, 4, 8, 16) for c in info["chunk"])
+    assert info["warps"] in (4, 6, 7, 8) and all(c in (1, 2, 4, 8, 16) for c in info["chunk"])
     mbbp.mbbp_decode_mixed(P, ios, 100, 0.625, mbbp.RULE_NMS, ws)
     torch.cuda.synchronize()
     _same(ios, _per_code(codes, synd, llrs, 100))
