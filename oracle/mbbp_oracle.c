@@ -19,9 +19,14 @@
  *                                 subtrees over several orders (Section III-A)
  *   or_bp_f64 / or_bp_f32         syndrome BP on one representation
  *                                 (Section II-B, Eqs. (2)-(3)), see bp_body.inc
+ *   or_bp_serial_f64 / _f32       the serial schedule of Section II-B
  *   or_fws                        Frequency-Weighted Scoring (Section III-B)
+ *   or_lms                        least-metric selector (Section III-A)
+ *   or_random_sets                random augmentation of Table II
  *   or_mbbp_decode_f64 / _f32     Algorithm 1 over a batch of syndromes
  *   or_judge                      logical-error test by GF(2) rank (Section IV)
+ *   or_wms_forward / _backward    weighted min-sum and its adjoint (FP64;
+ *                                 not in the paper, reduces to Eq. (2)-(3))
  *
  * Parity of normalized min-sum with alpha < 1 on loopy graphs is unpinned by
  * the paper (no printed values); the tests pin BP through trees, where it is
