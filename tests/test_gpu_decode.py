@@ -257,3 +257,46 @@ def test_sum_product_against_fp32_oracle(M):
         assert same.mean() > 0.99
         err = np.abs(got["posterior"][same] - ref["post"][same]) / np.maximum(np.abs(ref["post"][same]), 1.0)
         assert err.max() <= 1e-4, (it, err.max())
+
+
+def test_graph_replayed_decode_exact(M):
+    """mbbp_decode captured once into a CUDA graph (the launch form of the
+    batched [[144]] benchmark) and replayed on new syndromes in the same
+    buffer: every output identical to the FP32 oracle on those syndromes."""
+    import torch
+    dev = torch.device("cuda:0")
+    c, H, _, s1 = workload("bb144", "HZ", 120, 0.06, "depolarizing")
+    _, _, _, s2 = workload("bb144", "HZ", 120, 0.06, "depolarizing", first=120)
+    B = M.mbbp_build_bases(H, 16, SEED + 1)
+    llr_np = channel_llr(144, 2 * 0.06 / 3).astype(np.float32)
+    llr = torch.from_numpy(llr_np).to(dev)
+    syn = torch.from_numpy(np.ascontiguousarray(s1)).to(dev)
+    out = {"e_hat": torch.empty((120, B.n), dtype=torch.uint8, device=dev),
+           "conv": torch.empty((120, B.R), dtype=torch.uint8, device=dev),
+           "iters": torch.empty((120, B.R), dtype=torch.int16, device=dev),
+           "success": torch.empty((120,), dtype=torch.uint8, device=dev),
+           "selected": torch.empty((120,), dtype=torch.int16, device=dev)}
+    ws = torch.empty((M.mbbp_decode_workspace_size(B, 120),), dtype=torch.uint8, device=dev)
+
+    def call(stream):
+        M.mbbp_decode(B, syn, llr, 100, 0.625, M.RULE_NMS, out["e_hat"], out["conv"], out["success"], ws,
+                      iters_run=out["iters"], selected=out["selected"], stream=stream)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        call(side)
+        side.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            call(side)
+    torch.cuda.current_stream().wait_stream(side)
+    for s in (s2, s1):
+        syn.copy_(torch.from_numpy(np.ascontiguousarray(s)))
+        graph.replay()
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        got["iters"] = got["iters"].view(np.uint16)
+        got["cand"] = M.unpack_words(ws[: 120 * B.R * B.words * 4].view(torch.int32).view(120, B.R, B.words), B.n)
+        ref = oracle.mbbp_decode(H, B.sets, s, llr_np, 100, 0.625, precision="f32")
+        assert_exact(got, ref)
