@@ -43,8 +43,8 @@ ALPHA = 0.625
 SEED = 20260515
 OPS_PER_EDGE_UPDATE = 10  # algorithmic ALU operations per edge-update (min-sum flooding)
 # DRAM bytes per shot of the BP kernel (ncu capture of a 100k-shot launch:
-# 7.31 MB read + 2.6 KB written); None once the kernel changes
-DRAM_BYTES_PER_SHOT = (7.311e6 + 2.56e3) / 100000
+# 7.37 MB read + 3.6 KB written); None once the kernel changes
+DRAM_BYTES_PER_SHOT = (7.370e6 + 3.58e3) / 100000
 WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
 
 
@@ -202,7 +202,8 @@ MIXED_P = 0.05
 def run_mixed(args):
     """[[72]], [[144]] and [[288]] shots 1:1:1 (R = 8 / 16 / 32), depolarizing
     p = 0.05, X and Z decoded: one autotuned, graph-captured mbbp_decode_mixed
-    per step (a persistent launch per kernel body) against one plain
+    per step (a persistent launch per kernel body and small-code shape)
+    against one plain
     mbbp_decode per (code, type) on the same syndromes (identical outputs,
     hence identical LER)."""
     import torch
@@ -262,7 +263,12 @@ def run_mixed(args):
         for i, (_, _, _, LZ, LX) in enumerate(entries):
             mbbp.mbbp_judge(LZ, errs[i][0], ios[2 * i]["e_hat"], None, counts[2 * i])
             mbbp.mbbp_judge(LX, errs[i][1], ios[2 * i + 1]["e_hat"], None, counts[2 * i + 1])
-        launches["mixed"] = 9 + 2 + len(bases) + 6  # sample+syndrome, BP (two bodies), FWS per entry, judge
+        # sample+syndrome, BP (the generic launch and one per small-code shape;
+        # each code here has its own shape), FWS per entry, judge
+        kinds = mbbp.mbbp_plan_info(P)["kind"]
+        small = {entries[j // 2][0].name for j, k in enumerate(kinds) if k == 0}
+        bp = len(small) + (1 if any(k == 1 for k in kinds) else 0)
+        launches["mixed"] = 9 + bp + len(bases) + 6
 
     def step_plain(k):
         sample(k)
@@ -301,7 +307,8 @@ def run_mixed(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "mixed batch: [[72,12,6]] R=8, [[144,12,12]] R=16, [[288,12,18]] R=32, "
                                "1:1:1, depolarizing p=0.05, X and Z decoded, 100 iters, persistent autotuned "
-                               "launches (one per kernel body) replayed as one CUDA graph", "shots_per_step": 3 * per_code,
+                               "launches (one per kernel body and small-code shape) replayed as one CUDA graph",
+                   "shots_per_step": 3 * per_code,
                    "alpha": ALPHA},
         "plain": {"value": shots / (ms_plain / 1e3), "unit": "shots/s", "ms_per_step": ms_plain / args.steps,
                   "launches_per_step": launches["plain"]},

@@ -255,14 +255,14 @@ mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndro
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
- * Mixed batches: several codes decoded by one persistent launch.
+ * Mixed batches: several codes decoded by persistent launches.
  * ---------------------------------------------------------------------- */
 
 /* A plan for decoding the shots of up to 8 codes together (Algorithm 1 for
  * each code's shots, as mbbp_decode).  The plan keeps the code handles
- * (which must outlive it) and its launch configuration: warps per block,
- * shots per work item and kernel path per code, and the order of the codes
- * in the work list (heaviest first by default). */
+ * (which must outlive it) and its launch configuration: warps per block of
+ * the generic-path launch, shots per work item and kernel path per code, and
+ * the order of the codes in the work list (heaviest first by default). */
 typedef struct mbbp_plan mbbp_plan;
 
 /* Inputs and outputs of one code in a mixed batch; the meaning, layout and
@@ -287,9 +287,10 @@ void mbbp_plan_free(mbbp_plan* P);
 size_t mbbp_plan_workspace_size(const mbbp_plan* P, const int32_t* batches);
 
 /* Decode io[c] (host array of n_codes entries) with code c of the plan: one
- * persistent BP launch per kernel body the plan uses (small-code path,
- * generic path; each with its own register budget) over every (code, shot
- * chunk, representation) work item of that body, then FWS per code.
+ * persistent BP launch per kernel body the plan uses (the generic path in
+ * blocks of the plan's warps, the small-code path once per shape in use, in
+ * one-warp blocks; each with its own register budget) over every (code, shot
+ * chunk, representation) work item of that launch, then FWS per code.
  * Outputs are identical to one mbbp_decode per
  * code.  Only kernel launches and a memset are enqueued, so the call can be
  * captured into a CUDA graph (after the first call with the same plan, shapes
@@ -299,15 +300,15 @@ mbbp_status mbbp_decode_mixed(const mbbp_plan* P, const mbbp_code_io* io, int it
                               int rule, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Choose the plan's launch configuration by timing mbbp_decode_mixed on the
- * given inputs (coordinate descent over warps per block in {4, 6, 7, 8}, shots per
- * work item in {1, 2, 4, 8, 16} and the kernel path per code, then the code
- * order).  Synchronises the stream, overwrites the outputs; not capturable.
+ * given inputs (coordinate descent over the generic launch's warps per block
+ * in {4, 6, 7, 8}, shots per work item in {1, 2, 4, 8, 16} and the kernel
+ * path per code, then the code order).  Synchronises the stream, overwrites the outputs; not capturable.
  * best_ms: host float or NULL, the time of the chosen configuration. */
 mbbp_status mbbp_plan_autotune(mbbp_plan* P, const mbbp_code_io* io, int iters, float alpha,
                                int rule, void* workspace, size_t workspace_bytes, void* stream,
                                float* best_ms);
 
-/* The plan's configuration: warps per block; per code (host int32[n_codes]
+/* The plan's configuration: warps per block (generic path); per code (host int32[n_codes]
  * each, or NULL) shots per work item, path (0 small-code, 1 generic) and the
  * work-list order. */
 mbbp_status mbbp_plan_info(const mbbp_plan* P, int32_t* warps, int32_t* chunk, int32_t* kind,

@@ -7,15 +7,11 @@
 namespace mbbp {
 namespace {
 
-constexpr int kSmallWarps = 8;
-constexpr int kChunk = 8;  // shots per work item of a warp (same representation)
-
-// Blocks per SM the register budget is sized for (measured: 3 blocks at 80
-// registers issue more instructions than they gain in occupancy).
-constexpr int kSmallMinBlocks = 2;
+constexpr int kSmallWarps = 1;  // warps per block: each warp works alone
+constexpr int kChunk = 8;       // shots per work item of a warp (same representation)
 
 template <int VS, int RS, int ORS, int RULE, bool REG>
-__global__ void __launch_bounds__(kSmallWarps * 32, kSmallMinBlocks)
+__global__ void __launch_bounds__(kSmallWarps * 32, small_min_blocks(RS, RULE))
 decode_small_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) float smsg[];
     const DevBases& B = a.B;

@@ -1046,6 +1046,7 @@ void mbbp_plan_free(mbbp_plan* P) { delete P; }
 
 size_t mbbp_plan_workspace_size(const mbbp_plan* P, const int32_t* batches) {
     if (!P || !batches) return 0;
+    static_assert(kMixedGroups * sizeof(unsigned long long) <= 256, "work counters");
     size_t total = 256;  // work counters
     for (size_t c = 0; c < P->codes.size(); ++c) {
         if (batches[c] < 0) return 0;
@@ -1091,9 +1092,10 @@ mbbp_status mixed_impl(const mbbp_plan* P, const mbbp_code_io* io, int iters, fl
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(MBBP_E_INVALID, "workspace must be 256-byte aligned");
     if (mbbp_status st = check_device(P->device)) return st;
-    // one launch per kernel body (small / generic), each with its own work
-    // list and counter; the launch holding the plan's first code goes first
-    MixedArgs args[2] = {};
+    // one launch per kernel body and small-code shape (group), each with its
+    // own work list and counter; the groups launch in the order their first
+    // codes have in the plan
+    MixedArgs args[kMixedGroups] = {};
     char* ws = static_cast<char*>(workspace);
     std::vector<uint32_t*> cand(nc);
     for (int c = 0; c < nc; ++c) {
@@ -1101,23 +1103,25 @@ mbbp_status mixed_impl(const mbbp_plan* P, const mbbp_code_io* io, int iters, fl
         ws += align256((size_t)batches[c] * P->codes[c]->R * P->codes[c]->W * 4);
     }
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(ws);
-    unsigned long long firsts[2] = {0, 0};
-    size_t wbytes[2] = {16, 16};
-    int slots[2] = {0, 0};
-    int launch_order[2] = {-1, -1};
+    unsigned long long firsts[kMixedGroups] = {};
+    size_t wbytes[kMixedGroups];
+    int slots[kMixedGroups] = {};
+    std::vector<int> launch_order;
+    for (int g = 0; g < kMixedGroups; ++g) wbytes[g] = 16;
     for (int oi = 0; oi < nc; ++oi) {
         const int c = P->order[oi];
         const mbbp_bases* B = P->codes[c];
         const mbbp_code_io& x = io[c];
         if (x.batch == 0) continue;
-        const int k = P->kind[c];
-        if (launch_order[0] < 0) launch_order[0] = k;
-        else if (launch_order[0] != k) launch_order[1] = k;
-        MixedArgs& a = args[k];
-        unsigned long long& first = firsts[k];
-        MixedCode& mc = a.codes[slots[k]++];
+        const bool small = P->kind[c] == kKindSmall && B->dev.shape >= 1 && B->dev.shape <= kNumSmallShapes;
+        const int g = small ? B->dev.shape : 0;
+        if (std::find(launch_order.begin(), launch_order.end(), g) == launch_order.end())
+            launch_order.push_back(g);
+        MixedArgs& a = args[g];
+        unsigned long long& first = firsts[g];
+        MixedCode& mc = a.codes[slots[g]++];
         mc.B = B->dev;
-        mc.kind = P->kind[c];
+        mc.kind = small ? kKindSmall : kKindGeneric;
         mc.chunk = P->chunk[c];
         mc.io.synd = x.syndromes;
         mc.io.llr = x.llr;
@@ -1131,20 +1135,21 @@ mbbp_status mixed_impl(const mbbp_plan* P, const mbbp_code_io* io, int iters, fl
         mc.io.post = nullptr;
         mc.first = first;
         first += (unsigned long long)((x.batch + mc.chunk - 1) / mc.chunk) * B->R;
-        wbytes[k] = std::max(wbytes[k], mixed_warp_bytes(B->dev, mc.kind));
+        wbytes[g] = std::max(wbytes[g], mixed_warp_bytes(B->dev, mc.kind));
     }
-    for (int k = 0; k < 2; ++k) {
-        args[k].n_codes = slots[k];
-        args[k].total = firsts[k];
-        args[k].warp_bytes = (uint32_t)((wbytes[k] + 15) & ~(size_t)15);
-        args[k].counter = counters + k;
-        if ((size_t)P->warps * args[k].warp_bytes > 200 * 1024)
+    for (int g = 0; g < kMixedGroups; ++g) {
+        args[g].n_codes = slots[g];
+        args[g].total = firsts[g];
+        args[g].warp_bytes = (uint32_t)((wbytes[g] + 15) & ~(size_t)15);
+        args[g].counter = counters + g;
+        const int warps = g == 0 ? P->warps : 1;
+        if ((size_t)warps * args[g].warp_bytes > 200 * 1024)
             return fail(MBBP_E_TOO_LARGE, "shared memory per block");
     }
-    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        const int k = launch_order[i];
-        if (k >= 0 && args[k].total > 0) e = launch_mixed(args[k], k, P->warps, rule, s, P->sm_count);
+    cudaError_t e = cudaMemsetAsync(counters, 0, kMixedGroups * sizeof(unsigned long long), s);
+    for (size_t i = 0; i < launch_order.size() && e == cudaSuccess; ++i) {
+        const int g = launch_order[i];
+        if (args[g].total > 0) e = launch_mixed(args[g], g, P->warps, rule, s, P->sm_count);
     }
     if (e != cudaSuccess) return cuda_fail(e, "mbbp_decode_mixed (BP)");
     for (int c = 0; c < nc; ++c) {

@@ -106,6 +106,17 @@ struct SmallShape {
 constexpr SmallShape kSmallShapes[] = {{3, 2, 2}, {5, 3, 3}, {5, 4, 3}};
 constexpr int kNumSmallShapes = 3;
 
+// Resident one-warp blocks per SM that the register budget of a small-code
+// kernel (decode_small.cu, decode_mixed.cu) is sized for.  Measured on
+// [[144]], R = 16: with 18, ptxas settles at 96 registers (20 resident warps
+// per SM) and the kernel runs 9% faster than with 8-warp blocks at 116
+// registers (16 warps per SM); tighter budgets (20 or 21 blocks), or 2-warp
+// blocks at 10, were slower.  Four row steps and the sum-product rule need
+// more registers: 16 keeps them unspilled.
+__host__ __device__ constexpr int small_min_blocks(int RS, int rule) {
+    return (RS <= 3 && rule == MBBP_RULE_NMS) ? 18 : 16;
+}
+
 // Inputs and per-representation outputs of one code's batch of shots.
 struct ShotIO {
     const uint8_t* synd;      // [batch][m]
@@ -166,7 +177,11 @@ struct MixedArgs {
     unsigned long long* counter;
 };
 size_t mixed_warp_bytes(const DevBases& B, int kind);
-cudaError_t launch_mixed(const MixedArgs& a, int kind, int warps, int rule, cudaStream_t s, int sm_count);
+// Launch groups of a mixed batch: 0 = the generic path (blocks of `warps`
+// warps), 1..kNumSmallShapes = the small-code path of that shape (one-warp
+// blocks).
+constexpr int kMixedGroups = 1 + kNumSmallShapes;
+cudaError_t launch_mixed(const MixedArgs& a, int group, int warps, int rule, cudaStream_t s, int sm_count);
 
 // Weighted min-sum forward / backward / decode (wms.cu).
 struct WmsArgs {

@@ -88,8 +88,8 @@ def test_bb144_nms_exact_r16(M, which):
 
 @pytest.mark.parametrize("R,shots", [(16, 150), (32, 60)])
 def test_bb288_nms_exact(M, R, shots):
-    """[[288,12,18]] (the largest small-code shape: 9 variable steps, up to
-    224 rows of H^(t)), depolarizing p = 0.07, 100 iterations."""
+    """[[288,12,18]] (the generic flooding path: more variables than the
+    register-resident kernel holds), depolarizing p = 0.07, 100 iterations."""
     c, H, e, s = workload("bb288", "HZ", shots, 0.07, "depolarizing")
     B = M.mbbp_build_bases(H, R, SEED + 2)
     llr = channel_llr(288, 2 * 0.07 / 3).astype(np.float32)
@@ -172,6 +172,42 @@ def test_irregular_code(M):
     llr = channel_llr(n, 0.04).astype(np.float32)
     got = gpu_decode(M, B, s, llr, 40, 0.7)
     assert_exact(got, oracle.mbbp_decode(H, sets, s, llr, 40, 0.7, precision="f32"))
+
+
+def _regular_code(n, m, wc, seed):
+    """Random H with column weight wc and row weight n wc / m, no repeated
+    entry in a row (sockets shuffled, then repaired by random swaps)."""
+    wr = n * wc // m
+    rng = np.random.default_rng(seed)
+    sock = rng.permutation(np.repeat(np.arange(n), wc)).reshape(m, wr)
+    for _ in range(100000):
+        bad = [r for r in range(m) if len(set(sock[r])) < wr]
+        if not bad:
+            break
+        i, r2, j = rng.integers(wr), rng.integers(m), rng.integers(wr)
+        sock[bad[0], i], sock[r2, j] = sock[r2, j], sock[bad[0], i]
+    H = np.zeros((m, n), np.uint8)
+    for r in range(m):
+        H[r, sock[r]] = 1
+    assert (H.sum(0) == wc).all() and (H.sum(1) == wr).all()
+    return H
+
+
+@pytest.mark.parametrize("n,m", [(160, 80), (150, 90)])
+def test_four_row_step_small_codes(M, n, m):
+    """Codes that fill the register-resident kernel's largest shape (up to
+    160 variables, 97..128 rows of H^(t)): column weight 3 with rows of
+    weight 6 (every row fills the width) and of weight 5 (per-row degrees)."""
+    H = _regular_code(n, m, 3, 5)
+    sets = oracle.collect_subtrees(H, 8, 3)
+    assert 96 < m + max(len(t) for t in sets) <= 128
+    rng = np.random.default_rng(n)
+    e = (rng.random((300, n)) < 0.05).astype(np.uint8)
+    s = oracle.syndrome(H, e)
+    B = M.mbbp_build_bases_from_sets(H, sets)
+    llr = channel_llr(n, 0.05).astype(np.float32)
+    got = gpu_decode(M, B, s, llr, 50, 0.625)
+    assert_exact(got, oracle.mbbp_decode(H, sets, s, llr, 50, 0.625, precision="f32"))
 
 
 def test_gb882_r64_max_size(M):
