@@ -3,6 +3,7 @@
 // (Eq. (4)) into the kernels' layout, the logical basis for the judge, and
 // argument checking for the launches.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -165,33 +166,46 @@ mbbp_status collect_impl(const Tanner& g, int R, uint64_t seed, std::vector<int3
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Small-code layout: ELL index sigma[r] of every row r of H^(t) and the
-// variable at every position (32 positions = one warp step of the variable
-// pass).  Edge j of row r lives in shared-memory bank (sigma[r] + rot(j)) & 31.
-// In the variable pass the 32 lanes of a step read the i-th edge of their
-// variables together; the cost of that access is the largest number of lanes
-// that hit one bank.  Simulated annealing over row swaps and swaps of
-// equal-degree variables between steps lowers the summed cost; any layout
-// gives the same results, only the bank conflicts change.
+// Small-code layout: ELL index sigma[r] of every row r of H^(t), the slot
+// s = slot[r][j] < deg(r) that holds the j-th edge of row r (j in H's column
+// order), and the variable at every position (32 positions = one warp step of
+// the variable pass).  Slot s of row r lives in shared-memory bank
+// (sigma[r] + rot(s)) & 31.  In the variable pass the 32 lanes of a step read
+// the i-th edge of their variables together; the cost of that access is the
+// largest number of lanes that hit one bank.  Simulated annealing over row
+// swaps, swaps of two edge slots within a row and swaps of equal-degree
+// variables between steps lowers the summed cost.  The normalized min-sum
+// check rule is symmetric in a row's edges (minima and sign parity are
+// exact), so any layout gives the same results; the sum-product rule adds
+// its terms in slot order, which moves its rounding by a few ulps.
 struct SmallLayout {
-    std::vector<int> sigma;  // ELL index of row r
-    std::vector<int> order;  // variable at position p
+    std::vector<int> sigma;               // ELL index of row r
+    std::vector<std::array<int, 6>> slot;  // slot of the j-th edge of row r
+    std::vector<int> order;               // variable at position p
 };
 
 SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, uint64_t seed) {
     const int M = (int)src.size();
     constexpr int DVX = 8;
     std::vector<std::vector<std::pair<int, int>>> ve(n);  // (row, j), ascending row
+    std::vector<std::array<int, 6>> ei(M);                 // edge index i of (r, j) in ve[v]
     for (int r = 0; r < M; ++r) {
         const auto& cols = g.rcols[src[r]];
-        for (int j = 0; j < (int)cols.size(); ++j) ve[cols[j]].push_back({r, j});
+        for (int j = 0; j < (int)cols.size(); ++j) {
+            ei[r][j] = (int)ve[cols[j]].size();
+            ve[cols[j]].push_back({r, j});
+        }
     }
     std::vector<std::vector<std::pair<int, int>>> re(M);  // (variable, edge index i)
     for (int v = 0; v < n; ++v)
         for (int i = 0; i < (int)ve[v].size(); ++i) re[ve[v][i].first].push_back({v, i});
     SmallLayout L;
     L.sigma.resize(M);
-    for (int r = 0; r < M; ++r) L.sigma[r] = r;
+    L.slot.resize(M);
+    for (int r = 0; r < M; ++r) {
+        L.sigma[r] = r;
+        for (int j = 0; j < 6; ++j) L.slot[r][j] = j;
+    }
     L.order.resize(n);
     for (int v = 0; v < n; ++v) L.order[v] = v;
     std::stable_sort(L.order.begin(), L.order.end(),
@@ -200,32 +214,68 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, ui
     for (int p = 0; p < n; ++p) posof[L.order[p]] = p;
     const int steps = (n + 31) / 32;
     std::vector<int> cnt((size_t)steps * DVX * 32, 0), mx((size_t)steps * DVX, 0);
-    auto bank = [&](int r, int j) { return (L.sigma[r] + slot_rot(j)) & 31; };
+    auto bank = [&](int r, int j) { return (L.sigma[r] + slot_rot(L.slot[r][j])) & 31; };
     auto cell = [&](int v, int i) { return (posof[v] >> 5) * DVX + i; };
     for (int v = 0; v < n; ++v)
         for (int i = 0; i < (int)ve[v].size(); ++i) ++cnt[(size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second)];
+    // cost of a cell: its largest bank count (the wavefronts of the access)
+    // first, then its colliding lane pairs, so that a move removing one
+    // collision of several is rewarded before the largest count drops
     auto remax = [&](int c) {
-        int x = 0;
-        for (int k = 0; k < 32; ++k) x = std::max(x, cnt[(size_t)c * 32 + k]);
-        mx[c] = x;
+        int x = 0, pairs = 0;
+        for (int k = 0; k < 32; ++k) {
+            const int q = cnt[(size_t)c * 32 + k];
+            x = std::max(x, q);
+            pairs += q * (q - 1) / 2;
+        }
+        mx[c] = x * 1024 + pairs;
     };
     long total = 0;
     for (int c = 0; c < steps * DVX; ++c) { remax(c); total += mx[c]; }
     std::vector<int> best_sigma = L.sigma, best_order = L.order;
+    std::vector<std::array<int, 6>> best_slot = L.slot;
     long best = total;
     uint64_t rs = seed;
     auto rnd = [&]() { rs += 0x9E3779B97F4A7C15ULL; uint64_t z = rs;
                        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
                        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL; return z ^ (z >> 31); };
     std::vector<int> cells;
-    const int iters = 12000;
+    const int iters = 100000;
     for (int it = 0; it < iters; ++it) {
         const double T = 0.6 * (1.0 - (double)it / iters) + 0.02;
         cells.clear();
         long before = 0, after = 0;
-        const bool row_move = (rnd() & 1) || steps == 1;
+        const int kind = (int)(rnd() % 3);  // 0: two rows, 1: two edge slots of a row, 2: two variables
+        const bool row_move = kind == 0 || (kind == 2 && steps == 1);
         int a = 0, b = 0;
-        if (row_move) {
+        if (kind == 1) {
+            const int r = (int)(rnd() % M);
+            const auto& cols = g.rcols[src[r]];
+            const int d = (int)cols.size();
+            const int ja = (int)(rnd() % d), jb = (int)(rnd() % d);
+            if (ja == jb) continue;
+            const int ca = cell(cols[ja], ei[r][ja]), cb = cell(cols[jb], ei[r][jb]);
+            cells.push_back(ca);
+            if (cb != ca) cells.push_back(cb);
+            for (int c : cells) before += mx[c];
+            auto swap_slots = [&]() {
+                --cnt[(size_t)ca * 32 + bank(r, ja)];
+                --cnt[(size_t)cb * 32 + bank(r, jb)];
+                std::swap(L.slot[r][ja], L.slot[r][jb]);
+                ++cnt[(size_t)ca * 32 + bank(r, ja)];
+                ++cnt[(size_t)cb * 32 + bank(r, jb)];
+            };
+            swap_slots();
+            for (int c : cells) { remax(c); after += mx[c]; }
+            const long dd = after - before;
+            const double u = (double)(rnd() >> 11) * (1.0 / 9007199254740992.0);
+            if (dd <= 0 || u < std::exp(-(double)dd / T)) {
+                total += dd;
+            } else {
+                swap_slots();
+                for (int c : cells) remax(c);
+            }
+        } else if (row_move) {
             a = (int)(rnd() % M);
             b = (int)(rnd() % M);
             if (a == b) continue;
@@ -291,10 +341,12 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, ui
         if (total < best) {
             best = total;
             best_sigma = L.sigma;
+            best_slot = L.slot;
             best_order = L.order;
         }
     }
     L.sigma = best_sigma;
+    L.slot = best_slot;
     L.order = best_order;
     return L;
 }
@@ -345,10 +397,16 @@ std::vector<int> serial_positions(const std::vector<std::vector<int>>& rcols, co
         for (int c : target_cells[r])
             for (int sh = 0; sh < CS; ++sh) cnt[(size_t)c * 32 + ((pos[r] + 4 * sh) & 31)] += d;
     };
+    // cost of a cell: its largest bank count first, then its colliding access
+    // pairs (as in the small-code layout)
     auto remax = [&](int c) {
-        int x = 0;
-        for (int k = 0; k < 32; ++k) x = std::max(x, cnt[(size_t)c * 32 + k]);
-        mx[c] = x;
+        int x = 0, pairs = 0;
+        for (int k = 0; k < 32; ++k) {
+            const int q = cnt[(size_t)c * 32 + k];
+            x = std::max(x, q);
+            pairs += q * (q - 1) / 2;
+        }
+        mx[c] = x * 1024 + pairs;
     };
     for (int r = 0; r < M; ++r) add(r, 1);
     for (int c = 0; c < ncell; ++c) remax(c);
@@ -587,8 +645,10 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
                 const auto& cols = g.rcols[src[r]];
                 const int sg = L.sigma[r];
                 rinfo2[(size_t)t * MP + sg] = (uint32_t)src[r] | ((uint32_t)cols.size() << 16);
-                for (int j = 0; j < (int)cols.size(); ++j)
-                    vs[cols[j]].push_back((uint16_t)(j * MP + (sg & ~31) + ((sg + slot_rot(j)) & 31)));
+                for (int j = 0; j < (int)cols.size(); ++j) {
+                    const int sj = L.slot[r][j];
+                    vs[cols[j]].push_back((uint16_t)(sj * MP + (sg & ~31) + ((sg + slot_rot(sj)) & 31)));
+                }
             }
             // byte offsets within a warp's message area; a missing edge (and
             // every edge of a padding position) points at the zero slot
