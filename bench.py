@@ -42,6 +42,15 @@ ITERS = 100
 ALPHA = 0.625
 SEED = 20260515
 OPS_PER_EDGE_UPDATE = 10  # algorithmic ALU operations per edge-update (min-sum flooding)
+# Of those, 7 (|q|, three min1/min2 updates, sign parity, output select, sign
+# apply) are min/max and logic operations, which a GB300 SM executes on its
+# alu pipe at 64 lanes per clock, and 3 (alpha product, posterior and
+# extrinsic adds) FP32 multiplies and adds on its fma pipe at 128 lanes per
+# clock; the SM issues 128 lanes per clock (pipe widths confirmed by the
+# library's throughput probes, mbbp_probe).
+ALU_OPS, FMA_OPS = 7, 3
+ALU_LANES, FMA_LANES, ISSUE_LANES = 64, 128, 128
+EDGE_UPDATES_PER_CLK_SM = min(ALU_LANES / ALU_OPS, FMA_LANES / FMA_OPS, ISSUE_LANES / OPS_PER_EDGE_UPDATE)
 # DRAM bytes per shot of the BP kernel (ncu capture of a 100k-shot launch:
 # 7.37 MB read + 3.6 KB written); None once the kernel changes
 DRAM_BYTES_PER_SHOT = (7.370e6 + 3.58e3) / 100000
@@ -731,7 +740,9 @@ def main():
     peaks, peak_kind = read_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
-    peak_ops = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    f_max = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    peak_ops = sm_count * OPS_PER_EDGE_UPDATE * EDGE_UPDATES_PER_CLK_SM * f_max
+    peak_ops_128 = sm_count * 128 * f_max  # every operation at the fma pipe's 128 lanes
     achieved_ops = OPS_PER_EDGE_UPDATE * edge_per_launch / (dec_avg_ms / 1000.0)
     cnt = counts.cpu().numpy()
     ks = kstats.cpu().numpy()
@@ -746,6 +757,8 @@ def main():
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(args.cpu_seconds)
+    clocks = clk.summary()
+    probe = measure_probes(mbbp, stream, sm_count, clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0))
 
     if rank == 0:
         line = {
@@ -778,10 +791,14 @@ def main():
                          "kernel": "mbbp_decode (BP + FWS)", "decode_ms_avg": dec_avg_ms,
                          "edge_updates_per_launch": edge_per_launch,
                          "ops_per_edge_update": OPS_PER_EDGE_UPDATE,
-                         "peak_basis": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                       f"({peak_kind} max SM clock)"},
+                         "peak_basis": f"{sm_count} SMs x {peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max "
+                                       f"SM clock) x {OPS_PER_EDGE_UPDATE} ops x min({ALU_LANES}/{ALU_OPS} alu, "
+                                       f"{FMA_LANES}/{FMA_OPS} fma, {ISSUE_LANES}/{OPS_PER_EDGE_UPDATE} issue) "
+                                       "edge-updates per SM per clock; pipe widths confirmed by the probes",
+                         "peak_128_lanes": peak_ops_128 / 1e12, "frac_128_lanes": achieved_ops / peak_ops_128,
+                         "probe": probe},
             "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk.summary(),
+            "clocks": clocks,
         }
         if e2e is not None:
             line["e2e"] = e2e
@@ -790,6 +807,30 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_probes(mbbp, stream, sm_count, mhz):
+    """Per-SM rates of the throughput probes (FP32 add, FP32 min/max, 3-input
+    logic: lanes per clock; 16-byte shared-memory loads: bytes per clock), the
+    best of three launches each, at the SM clock sampled during the timed
+    region."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float32, device=stream.device)
+    out = {}
+    for kind, name in ((mbbp.PROBE_FADD, "fadd_lanes"), (mbbp.PROBE_FMNMX, "fmnmx_lanes"),
+                       (mbbp.PROBE_LOP3, "lop3_lanes"), (mbbp.PROBE_SMEM, "smem_bytes")):
+        mbbp.mbbp_probe(kind, 64, sink, stream=stream)
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            work = mbbp.mbbp_probe(kind, 2048, sink, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, work / (e0.elapsed_time(e1) * 1e-3) / sm_count / (mhz * 1e6))
+        out[name + "_per_clk_per_sm"] = round(best, 2)
+    out["sm_mhz"] = mhz
+    return out
 
 
 def run_e2e(args, mbbp, BZ, BX, llrs, S, dev, stream, rank, world):

@@ -426,6 +426,26 @@ mbbp_status mbbp_judge(const mbbp_logicals* L, int batch, const uint32_t* e,
 /* Free a logicals handle (NULL is a no-op). */
 void mbbp_logicals_free(mbbp_logicals* L);
 
+/* ------------------------------------------------------------------------
+ * Throughput probes (measurement; no counterpart in the paper).
+ * ---------------------------------------------------------------------- */
+
+/* Probe kinds: FP32 add, FP32 min/max, 3-input logic (the operation classes
+ * of the BP update rules, Eq. (2)-(3)), and 16-byte shared-memory loads. */
+enum { MBBP_PROBE_FADD = 0, MBBP_PROBE_FMNMX = 1, MBBP_PROBE_LOP3 = 2, MBBP_PROBE_SMEM = 3 };
+
+/* Enqueue one launch of probe `kind` on `stream`: every SM full of
+ * 1024-thread blocks, each thread running `rounds` rounds of 64 operations
+ * (8 interdependent chains, so none can be merged away) or of eight 16-byte
+ * shared-memory loads at conflict-free addresses.  *work (host, written
+ * before the launch runs) = the lane operations, or the shared-memory bytes,
+ * that the launch performs; the caller times the launch (CUDA events on
+ * `stream`) to get the per-SM rate behind the BP kernels' roofline.  sink:
+ * device float[1], written only if a chain ends equal to 1e-30, which does
+ * not happen (it keeps the work alive).  MBBP_E_INVALID for an unknown kind,
+ * rounds < 1 or a NULL pointer. */
+mbbp_status mbbp_probe(int kind, int rounds, float* sink, double* work, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

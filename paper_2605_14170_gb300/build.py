@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmbbp.so")
 SOURCES = ["host.cpp", "decode.cu", "decode_small.cu", "decode_serial.cu", "decode_mixed.cu", "wms.cu",
-           "aux.cu"]
+           "aux.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

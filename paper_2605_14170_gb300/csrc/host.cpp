@@ -1545,6 +1545,13 @@ mbbp_status mbbp_logicals_info(const mbbp_logicals* L, int32_t* k, uint8_t* ops)
     return MBBP_OK;
 }
 
+mbbp_status mbbp_probe(int kind, int rounds, float* sink, double* work, void* stream) {
+    if (kind < MBBP_PROBE_FADD || kind > MBBP_PROBE_SMEM) return fail(MBBP_E_INVALID, "mbbp_probe: unknown kind");
+    if (rounds < 1 || !sink || !work) return fail(MBBP_E_INVALID, "mbbp_probe: bad arguments");
+    const cudaError_t e = launch_probe(kind, rounds, sink, (cudaStream_t)stream, work);
+    return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_probe");
+}
+
 mbbp_status mbbp_judge(const mbbp_logicals* L, int batch, const uint32_t* e, const uint8_t* e_hat,
                        uint8_t* fail_out, unsigned long long* counts, void* stream) {
     if (!L || batch < 0) return fail(MBBP_E_INVALID, "mbbp_judge: bad arguments");

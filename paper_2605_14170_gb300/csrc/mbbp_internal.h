@@ -225,6 +225,9 @@ cudaError_t static_scratch(void** ptr);
 // Sets the dynamic shared-memory limit of a kernel and returns its blocks per
 // SM, once per (kernel, block size, shared memory, device); cached afterwards.
 cudaError_t prepare_kernel(const void* func, int threads, size_t smem, int* blocks_per_sm);
+// Throughput probe (probe.cu): one launch of probe `kind` (MBBP_PROBE_*);
+// *work = its lane operations or shared-memory bytes.
+cudaError_t launch_probe(int kind, int rounds, float* sink, cudaStream_t s, double* work);
 cudaError_t launch_sample(int n, int batch, uint64_t first_shot, uint64_t seed, uint64_t T,
                           int noise, uint32_t* ex, uint32_t* ez, cudaStream_t s);
 cudaError_t launch_syndrome(const DevBases& B, int batch, const uint32_t* e, uint8_t* synd,

@@ -28,6 +28,10 @@ DECISION_FWS = 0
 DECISION_LMS = 1
 NOISE_BSC = 0
 NOISE_DEPOLARIZING = 1
+PROBE_FADD = 0
+PROBE_FMNMX = 1
+PROBE_LOP3 = 2
+PROBE_SMEM = 3
 MAX_R = 64
 LMAX = 1.0e4
 SP_MAX = 16.635532
@@ -105,6 +109,7 @@ _sig = {
     "mbbp_logicals_info": (C.c_int, [_vp, _vp, _vp]),
     "mbbp_judge": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "mbbp_logicals_free": (None, [_vp]),
+    "mbbp_probe": (C.c_int, [C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -645,3 +650,15 @@ def pack_bits(bits) -> np.ndarray:
     pad[..., :n] = bits
     w = (pad.reshape(bits.shape[:-1] + (W, 32)).astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(-1)
     return w.astype(np.uint32).view(np.int32)
+
+
+# ---------------------------------------------------------------- probes
+
+def mbbp_probe(kind: int, rounds: int, sink, stream=None) -> float:
+    """Enqueue one throughput-probe launch; returns its work (lane operations,
+    or shared-memory bytes for PROBE_SMEM).  sink: CUDA float32 tensor [1]."""
+    import torch
+    work = C.c_double(0.0)
+    _check(_lib.mbbp_probe(kind, rounds, _dptr(sink, torch.float32, "sink"), C.byref(work), _stream(stream)),
+           "mbbp_probe")
+    return work.value

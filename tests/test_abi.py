@@ -46,6 +46,15 @@ def test_version_and_error_string(lib):
     assert "bad arguments" in lib.mbbp_last_error()
 
 
+def test_probe_rejects_bad_arguments(lib):
+    """The throughput probe checks its arguments before any CUDA call."""
+    import ctypes as C
+    work = C.c_double(0.0)
+    assert lib._lib.mbbp_probe(9, 1, None, C.byref(work), None) == 1
+    assert "unknown kind" in lib.mbbp_last_error()
+    assert lib._lib.mbbp_probe(lib.PROBE_FADD, 0, None, C.byref(work), None) == 1
+
+
 def test_fig2_example_host(lib):
     H = np.array([[1, 1, 1, 0, 0, 0], [0, 1, 1, 0, 0, 1], [1, 0, 0, 1, 1, 0], [0, 0, 0, 1, 1, 1]], np.uint8)
     cs, order, ns = lib.mbbp_subtrees(H, np.array([0, 3, 1, 2]))
