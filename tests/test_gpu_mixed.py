@@ -111,3 +111,40 @@ def test_mixed_with_an_empty_code():
     torch.cuda.synchronize()
     ref = mbbp.decode(codes[1][1], synd[1], llrs[1], 50, 0.625)
     assert torch.equal(ios[1]["e_hat"], ref["e_hat"]) and torch.equal(ios[1]["iters"], ref["iters"])
+
+
+def test_mixed_launch_groups_per_shape():
+    """A plan whose small codes have different register-resident shapes
+    ([[72]]; a random column-weight-3 code with 97..128 rows of H^(t)) and a
+    generic-path code: one launch per shape plus the generic launch, outputs
+    identical to one mbbp_decode per code and, for the four-row-step code, to
+    the FP32 oracle."""
+    import torch
+    from paper_2605_14170_gb300 import mbbp
+    rng = np.random.default_rng(21)
+    n, m = 160, 80
+    sock = rng.permutation(np.repeat(np.arange(n), 3)).reshape(m, 6)
+    for _ in range(100000):
+        bad = [r for r in range(m) if len(set(sock[r])) < 6]
+        if not bad:
+            break
+        i, r2, j = rng.integers(6), rng.integers(m), rng.integers(6)
+        sock[bad[0], i], sock[r2, j] = sock[r2, j], sock[bad[0], i]
+    H4 = np.zeros((m, n), np.uint8)
+    for r in range(m):
+        H4[r, sock[r]] = 1
+    sets4 = oracle.collect_subtrees(H4, 6, 9)
+    assert 96 < m + max(len(t) for t in sets4) <= 128
+    codes = [c for c in _codes() if c[0].shape[1] in (72, 288)]
+    codes.append((H4, mbbp.mbbp_build_bases_from_sets(H4, sets4), 400, 0.05))
+    P = mbbp.mbbp_plan_create([B for _, B, _, _ in codes])
+    assert mbbp.mbbp_plan_info(P)["kind"] == [0, 1, 0]
+    synd, llrs = _inputs(codes, 17)
+    ios, ws = mbbp.mixed_buffers(P, synd, llrs)
+    mbbp.mbbp_decode_mixed(P, ios, 60, 0.625, mbbp.RULE_NMS, ws)
+    torch.cuda.synchronize()
+    _same(ios, _per_code(codes, synd, llrs, 60))
+    s = synd[2].cpu().numpy()
+    ref = oracle.mbbp_decode(H4, sets4, s, llrs[2].cpu().numpy(), 60, 0.625, precision="f32")
+    assert np.array_equal(ios[2]["e_hat"].cpu().numpy(), ref["ehat"])
+    assert np.array_equal(ios[2]["iters"].cpu().numpy().view(np.uint16), ref["iters"])
