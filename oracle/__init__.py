@@ -124,6 +124,10 @@ def _load():
             lib.or_lms.argtypes = [u8p, u8p, C.c_int, C.c_int, f32p, u8p, C.POINTER(C.c_int)]
             lib.or_random_sets.restype = None
             lib.or_random_sets.argtypes = [C.c_int, C.c_int, i32p, C.c_uint64, i32p, i32p]
+            lib.or_clamp_reset.restype = None
+            lib.or_clamp_reset.argtypes = []
+            lib.or_clamp_stats.restype = None
+            lib.or_clamp_stats.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
             lib.or_judge.restype = None
             lib.or_judge.argtypes = [u8p, C.c_int, u8p, C.c_int, C.c_int, C.c_int,
                                      u8p, u8p, u8p]
@@ -246,6 +250,19 @@ def bp(Ht, st, mu, iters: int, alpha: float, rule: int = RULE_NMS,
     if want_c2v:
         out["c2v"] = c2v
     return out
+
+
+def clamp_reset() -> None:
+    """Zero this thread's clamp counters (see clamp_stats)."""
+    _load().or_clamp_reset()
+
+
+def clamp_stats():
+    """(v->c messages computed, messages clamped to +-LMAX) by this thread's
+    BP calls (flooding and serial, both precisions) since clamp_reset."""
+    total, clamped = C.c_longlong(0), C.c_longlong(0)
+    _load().or_clamp_stats(C.byref(total), C.byref(clamped))
+    return int(total.value), int(clamped.value)
 
 
 def fws(cand, conv):

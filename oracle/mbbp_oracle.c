@@ -27,6 +27,8 @@
  *   or_judge                      logical-error test by GF(2) rank (Section IV)
  *   or_wms_forward / _backward    weighted min-sum and its adjoint (FP64;
  *                                 not in the paper, reduces to Eq. (2)-(3))
+ *   or_clamp_reset, or_clamp_stats  how often BP's message clamp acts (a
+ *                                 diagnostic of the clamp reading)
  *
  * Parity of normalized min-sum with alpha < 1 on loopy graphs is unpinned by
  * the paper (no printed values); the tests pin BP through trees, where it is
@@ -41,6 +43,16 @@
 #define OR_RULE_SP 1
 /* Message clamp (not stated in the paper; see bp_body.inc). */
 #define OR_LMAX 1.0e4
+
+/* How often the clamp acts: v->c messages computed and messages clamped, by
+ * the BP calls of the calling thread since its last or_clamp_reset (a
+ * diagnostic; the counts do not enter any result). */
+static _Thread_local long long or_q_total, or_q_clamped;
+void or_clamp_reset(void) { or_q_total = 0; or_q_clamped = 0; }
+void or_clamp_stats(long long* total, long long* clamped) {
+    *total = or_q_total;
+    *clamped = or_q_clamped;
+}
 /* Sum-product magnitude clamp: 2 atanh(1 - 2^-23) = ln(2^24 - 1). */
 #define OR_SPMAX 16.635532333438686
 
