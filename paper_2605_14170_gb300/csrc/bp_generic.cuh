@@ -218,7 +218,9 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
     int K = 0;
     bool conv = false;
     for (int it = 0;; ++it) {
-        // halting rule: H e = s on the rows of H (the extra rows are copies)
+        // halting rule: H e = s on the rows of H (the extra rows are copies);
+        // the first row group decides most unconverged iterations, so the
+        // other groups are tested only if it passed
         bool ok = true;
         for (int k = 0; k < orow_steps; ++k) {
             const int r = lane + 32 * k;
@@ -227,6 +229,10 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
 #pragma unroll
                 for (int j = 0; j < DC; ++j) par ^= eh[hcol[j * mpad + r]];
                 ok = ok && (par == 0u);
+            }
+            if (k == 0 && orow_steps > 1) {  // warp-uniform condition
+                const bool first_ok = __all_sync(kFull, ok);
+                if (!first_ok) break;
             }
         }
         if (__all_sync(kFull, ok)) {
@@ -320,7 +326,7 @@ __device__ __forceinline__ void run_item_serial(const DevBases& B, const ShotIO&
     int K = 0;
     bool conv = false;
     for (int it = 0;; ++it) {
-        bool ok = true;
+        bool ok = true;  // halting rule, first row group first (as in run_item)
         for (int k = 0; k < orow_steps; ++k) {
             const int r = lane + 32 * k;
             if (r < m) {
@@ -328,6 +334,10 @@ __device__ __forceinline__ void run_item_serial(const DevBases& B, const ShotIO&
 #pragma unroll
                 for (int j = 0; j < DC; ++j) par ^= eh[hcol[j * mpad + r]];
                 ok = ok && (par == 0u);
+            }
+            if (k == 0 && orow_steps > 1) {  // warp-uniform condition
+                const bool first_ok = __all_sync(kFull, ok);
+                if (!first_ok) break;
             }
         }
         if (__all_sync(kFull, ok)) {

@@ -97,17 +97,25 @@ __device__ __forceinline__ void load_shot(const DevBases& B, const ShotIO& io, i
 }
 
 // Halting rule of the shot in slot sh: H e = s on the rows of H (the extra
-// rows of H^(t) are copies).  Warp-uniform result.
+// rows of H^(t) are copies), the first row group first.  Warp-uniform result.
 template <int DC>
 __device__ __forceinline__ bool halted(int m, int mpad, const uint16_t* hcol, const uint8_t* e,
                                        const uint32_t* sb) {
     const int lane = threadIdx.x & 31;
     bool ok = true;
-    for (int r = lane; r < m; r += 32) {
-        uint32_t par = (sb[r >> 5] >> (r & 31)) & 1u;
+    for (int r0 = 0; r0 < m; r0 += 32) {
+        const int r = r0 + lane;
+        if (r < m) {
+            uint32_t par = (sb[r >> 5] >> (r & 31)) & 1u;
 #pragma unroll
-        for (int j = 0; j < DC; ++j) par ^= e[hcol[j * mpad + r]];
-        ok = ok && (par == 0u);
+            for (int j = 0; j < DC; ++j) par ^= e[hcol[j * mpad + r]];
+            ok = ok && (par == 0u);
+        }
+        // the first row group decides most unconverged iterations
+        if (r0 == 0 && m > 32) {  // warp-uniform condition
+            const bool first_ok = __all_sync(kFull, ok);
+            if (!first_ok) return false;
+        }
     }
     return __all_sync(kFull, ok);
 }
