@@ -113,7 +113,12 @@ __device__ __forceinline__ void check_row(float* msg, int r, int MP, int deg, ui
 }
 
 // Variable-node update of a degree-D variable (Eq. (3)): q_i = mu + sum of
-// the other messages in ascending row order, clamped; returns the posterior.
+// the other messages in ascending row order; returns the posterior.  The
+// clamp of q to [-LMAX, LMAX] is not applied because nothing observable
+// depends on it: q only feeds the check rule, whose min also runs over LMAX
+// (so |q| >= LMAX and LMAX give the same message and sign), and phi(|q|)
+// underflows to 0 for |q| >= 104 under either value; q stays finite
+// (|q| <= |mu| + 12 LMAX).
 template <int D>
 __device__ __forceinline__ float var_update(float* msg, const uint16_t* __restrict__ sl,
                                             float mu) {
@@ -132,7 +137,7 @@ __device__ __forceinline__ float var_update(float* msg, const uint16_t* __restri
         float q = P[i];
 #pragma unroll
         for (int k = i + 1; k < D; ++k) q = __fadd_rn(q, m[k]);
-        msg[s[i]] = fminf(fmaxf(q, -MBBP_LMAX), MBBP_LMAX);
+        msg[s[i]] = q;
     }
     return P[D];
 }
@@ -370,7 +375,7 @@ __device__ __forceinline__ void run_item_serial(const DevBases& B, const ShotIO&
                                 if (sl != slot) x = __fadd_rn(x, msg[sl]);
                             }
                         }
-                        q[j] = fminf(fmaxf(x, -MBBP_LMAX), MBBP_LMAX);
+                        q[j] = x;  // unclamped, as in var_update
                     }
                 }
                 check_out<DC, RULE>(q, msg, r, MP, deg, (sbits[r >> 5] >> (r & 31)) & 1u, io.alpha);

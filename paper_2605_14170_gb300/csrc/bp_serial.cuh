@@ -33,7 +33,9 @@ __device__ __forceinline__ float lds_b(const float* base, uint32_t byte_off) {
 }
 
 // The q_{v->c} of one edge: mu_v plus NO other messages of v (byte offsets
-// in the descriptor; unused ones point at the -0.0f slot), clamped.
+// in the descriptor; unused ones point at the -0.0f slot).  Unclamped: q only
+// feeds check_out, whose min runs over LMAX and whose sum-product phi
+// underflows to 0 beyond |q| = 104, so a clamp changes no message.
 template <int NO>
 __device__ __forceinline__ float edge_q(const float* msg, const float* mu, uint4 d) {
     const uint32_t o[7] = {d.x >> 16, d.y & 0xffffu, d.y >> 16, d.z & 0xffffu, d.z >> 16,
@@ -41,7 +43,7 @@ __device__ __forceinline__ float edge_q(const float* msg, const float* mu, uint4
     float x = mu[d.x & 0xffffu];
 #pragma unroll
     for (int i = 0; i < NO; ++i) x = __fadd_rn(x, lds_b(msg, o[i]));
-    return fminf(fmaxf(x, -MBBP_LMAX), MBBP_LMAX);
+    return x;
 }
 
 // Posterior of one variable: mu_v plus its NV message slots (padded).
