@@ -16,9 +16,13 @@
 // (__fadd_rn / __fmul_rn) in the order the oracle uses: variable sums in
 // ascending row order of H^(t) excluding the own edge, sum-product phi sums
 // in ascending column order excluding the own edge.  Min-sum takes its min
-// over the other edges and MBBP_LMAX with a min1/min2 pair, which gives the
-// same value as the direct min.  Hence normalized min-sum reproduces the FP32
-// oracle bit for bit; sum-product differs only through expm1f/log1pf.
+// over the other edges and MBBP_LMAX from prefix and suffix minima (exact),
+// then one correctly rounded alpha product per edge.  Signs come from the
+// sign bits: the LLRs enter as mu + 0 (turning -0 into +0) and every q is a
+// sum that starts from mu, so no q is -0 and its sign bit is set exactly
+// when q < 0, the oracle's sign rule.  Hence normalized min-sum reproduces
+// the FP32 oracle bit for bit; sum-product differs only through
+// expm1f/log1pf.
 #pragma once
 
 #include "mbbp_internal.h"
@@ -57,23 +61,26 @@ template <int DC, int RULE>
 __device__ __forceinline__ void check_out(const float (&q)[DC], float* msg, int r, int MP, int deg,
                                           uint32_t sbit, float alpha) {
     if (RULE == MBBP_RULE_NMS) {
-        float min1 = MBBP_LMAX, min2 = MBBP_LMAX;
-        uint32_t par = sbit;
+        // sign parity of the row (syndrome bit included) from the sign bits
+        uint32_t sx = sbit << 31;
 #pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            const float x = fabsf(q[j]);
-            min2 = fminf(min2, fmaxf(min1, x));
-            min1 = fminf(min1, x);
-            par ^= (q[j] < 0.f) ? 1u : 0u;
-        }
-        const float am1 = __fmul_rn(alpha, min1);
-        const float am2 = __fmul_rn(alpha, min2);
+        for (int j = 0; j < DC; ++j) sx ^= __float_as_uint(q[j]);
+        sx &= 0x80000000u;
+        // min over the other edges and LMAX: prefix and suffix minima
+        float pre[DC], suf[DC];
+        pre[0] = MBBP_LMAX;
+#pragma unroll
+        for (int j = 1; j < DC; ++j) pre[j] = fminf(pre[j - 1], fabsf(q[j - 1]));
+        suf[DC - 1] = MBBP_LMAX;
+#pragma unroll
+        for (int j = DC - 2; j >= 0; --j)
+            suf[j] = (j == DC - 2) ? fabsf(q[DC - 1]) : fminf(suf[j + 1], fabsf(q[j + 1]));
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
             if (j < deg) {
-                const float mag = (fabsf(q[j]) == min1) ? am2 : am1;
-                const uint32_t neg = par ^ ((q[j] < 0.f) ? 1u : 0u);
-                msg[j * MP + r] = neg ? -mag : mag;
+                const float excl = (j == DC - 1) ? pre[j] : (j == 0 ? fminf(MBBP_LMAX, suf[0]) : fminf(pre[j], suf[j]));
+                const uint32_t mag = __float_as_uint(__fmul_rn(alpha, excl));
+                msg[j * MP + r] = __uint_as_float(mag ^ ((sx ^ __float_as_uint(q[j])) & 0x80000000u));
             }
         }
     } else {
@@ -200,7 +207,7 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
     // channel LLRs, hard decision of the LLRs, syndrome bits of my rows
     for (int v = lane; v < n; v += 32) {
         const float x = __ldg(llr + v);
-        mu_s[v] = x;
+        mu_s[v] = __fadd_rn(x, 0.0f);  // -0 -> +0 (sign bits decide the check rule)
         eh[v] = (x < 0.f) ? 1 : 0;
     }
     if (lane == 0) eh[n] = 0;  // padding column of hcol
@@ -312,7 +319,7 @@ __device__ __forceinline__ void run_item_serial(const DevBases& B, const ShotIO&
     __syncwarp();
     for (int v = lane; v < n; v += 32) {
         const float x = __ldg(llr + v);
-        mu_s[v] = x;
+        mu_s[v] = __fadd_rn(x, 0.0f);  // -0 -> +0 (sign bits decide the check rule)
         eh[v] = (x < 0.f) ? 1 : 0;
         if (io.post) io.post[item * n + v] = x;
     }

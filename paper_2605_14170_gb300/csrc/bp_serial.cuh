@@ -77,7 +77,7 @@ __device__ __forceinline__ void load_shot(const DevBases& B, const ShotIO& io, i
     if (lane == 0) ms[DC * MP] = -0.0f;
     for (int v = lane; v < n; v += 32) {
         const float x = __ldg(llr + v);
-        mu[sh * L.NP + v] = x;
+        mu[sh * L.NP + v] = __fadd_rn(x, 0.0f);  // -0 -> +0 (sign bits decide the check rule)
         eh[sh * L.EP + v] = (x < 0.f) ? 1 : 0;
         if (io.post) io.post[item * n + v] = x;
     }
