@@ -38,6 +38,19 @@ def _setup(code="bb72", R=2, shots=12, T=8, seed=1, p=0.07):
     return H, B, s, ex, mu, w, g, t
 
 
+def _same_sums(a, b, rel=1e-4):
+    """Two launches' weight / damping gradients.  The backward kernel adds
+    each (shot, representation) item's terms with float atomics, so the
+    summation order, and with it the last bits, varies from launch to
+    launch: two orders of the same N terms differ by at most 2 N u sum|terms|
+    (u = 2^-24), which bounds their difference in norm, not elementwise
+    (an element whose terms cancel can differ by more than its own size
+    times 1e-5).  An error in what is summed changes the norm by O(1)."""
+    a = np.asarray(a.cpu().numpy() if hasattr(a, "cpu") else a, np.float64)
+    b = np.asarray(b.cpu().numpy() if hasattr(b, "cpu") else b, np.float64)
+    assert np.linalg.norm(a - b) <= rel * np.linalg.norm(b) + 1e-12, (np.linalg.norm(a - b), np.linalg.norm(b))
+
+
 def _oracle_item(H, B, s, mu, w, g, e, shot, b, scale):
     rows = B.sets[b]
     Ht = np.concatenate([H, H[rows]])
@@ -161,8 +174,8 @@ def test_checkpoint_interval_does_not_change_gradients():
         res.append((post.clone(), gw, gg))
     for post, gw, gg in res[1:]:
         assert torch.equal(post, res[0][0])
-        torch.testing.assert_close(gw, res[0][1], rtol=1e-5, atol=1e-6)
-        torch.testing.assert_close(gg, res[0][2], rtol=1e-5, atol=1e-6)
+        _same_sums(gw, res[0][1])
+        _same_sums(gg, res[0][2])
 
 
 def test_segment_states_in_global_memory_match_shared_memory():
@@ -199,8 +212,8 @@ def test_segment_states_in_global_memory_match_shared_memory():
     for gw, gg in res:
         for got, ref in ((gw, gw_ref), (gg, gg_ref)):
             assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
-    np.testing.assert_allclose(res[0][0], res[1][0], rtol=1e-4, atol=1e-9)
-    np.testing.assert_allclose(res[0][1], res[1][1], rtol=1e-4, atol=1e-9)
+    _same_sums(res[0][0], res[1][0])
+    _same_sums(res[0][1], res[1][1])
 
 
 def test_autograd_function_and_adam():
@@ -219,8 +232,8 @@ def test_autograd_function_and_adam():
     gw = torch.zeros_like(t["w"])
     gg = torch.zeros_like(t["g"])
     mbbp.mbbp_wms_backward(B, t["s"], t["mu"], T, t["w"], t["g"], 2, t["e"], scale, post, gw, gg, ws, all_iters=True)
-    torch.testing.assert_close(wt.grad, gw, rtol=1e-5, atol=1e-8)
-    torch.testing.assert_close(gt.grad, gg, rtol=1e-5, atol=1e-8)
+    _same_sums(wt.grad, gw)
+    _same_sums(gt.grad, gg)
     # Adam against its definition (Kingma & Ba), clamped to [lo, hi]
     rng = np.random.default_rng(0)
     p0 = rng.uniform(0, 1, 1000).astype(np.float32)
