@@ -265,9 +265,12 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
             }
         }
         __syncwarp();
-        // variable pass, posterior, hard decision
+        // variable pass, posterior, hard decision; each step's descriptor is
+        // loaded one step ahead, so only the slot-list load waits on L1
+        uint2 dn = (lane < n) ? __ldg(vd + lane) : make_uint2(0u, 0u);
         for (int p = lane; p < n; p += 32) {
-            const uint2 d = __ldg(vd + p);
+            const uint2 d = dn;
+            if (p + 32 < n) dn = __ldg(vd + p + 32);
             const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
             const float post = var_dispatch<1, DV>(deg, msg, B.vslot + d.x, mu_s[v]);
             eh[v] = (post < 0.f) ? 1 : 0;
