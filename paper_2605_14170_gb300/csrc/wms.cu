@@ -49,22 +49,40 @@ __host__ __device__ inline WmsLayout wms_layout(int DC, int MP, int n, int ckpt)
 }
 
 // q^(t)_e and the posterior from m (variable pass, ascending row order).
+// Each step's descriptor is loaded one step ahead; a variable's slots and
+// messages are read once into registers (at most DV of them).
 template <int DV>
 __device__ __forceinline__ void wms_var_pass(const DevBases& B, const uint2* vd, const float* m,
                                              float* q, const float* mu, float* post) {
     const int lane = threadIdx.x & 31;
-    for (int p = lane; p < B.n; p += 32) {
-        const uint2 d = __ldg(vd + p);
+    const int n = B.n;
+    uint2 dn = (lane < n) ? __ldg(vd + lane) : make_uint2(0u, 0u);
+    for (int p = lane; p < n; p += 32) {
+        const uint2 d = dn;
+        if (p + 32 < n) dn = __ldg(vd + p + 32);
         const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
         const uint16_t* sl = B.vslot + d.x;
+        int s[DV];
+        float mv[DV];
+#pragma unroll
+        for (int i = 0; i < DV; ++i) {
+            s[i] = (i < deg) ? (int)__ldg(sl + i) : 0;
+            mv[i] = (i < deg) ? m[s[i]] : 0.0f;
+        }
         float acc = mu[v];
-        for (int i = 0; i < deg; ++i) acc = __fadd_rn(acc, m[__ldg(sl + i)]);
+#pragma unroll
+        for (int i = 0; i < DV; ++i)
+            if (i < deg) acc = __fadd_rn(acc, mv[i]);
         if (post) post[v] = acc;
-        for (int i = 0; i < deg; ++i) {
-            float x = mu[v];
-            for (int k = 0; k < deg; ++k)
-                if (k != i) x = __fadd_rn(x, m[__ldg(sl + k)]);
-            q[__ldg(sl + i)] = x;
+#pragma unroll
+        for (int i = 0; i < DV; ++i) {
+            if (i < deg) {
+                float x = mu[v];
+#pragma unroll
+                for (int k = 0; k < DV; ++k)
+                    if (k < deg && k != i) x = __fadd_rn(x, mv[k]);
+                q[s[i]] = x;
+            }
         }
     }
 }
