@@ -51,9 +51,10 @@ OPS_PER_EDGE_UPDATE = 10  # algorithmic ALU operations per edge-update (min-sum 
 ALU_OPS, FMA_OPS = 7, 3
 ALU_LANES, FMA_LANES, ISSUE_LANES = 64, 128, 128
 EDGE_UPDATES_PER_CLK_SM = min(ALU_LANES / ALU_OPS, FMA_LANES / FMA_OPS, ISSUE_LANES / OPS_PER_EDGE_UPDATE)
-# DRAM bytes per shot of the BP kernel (ncu capture of a 100k-shot launch:
-# 7.37 MB read + 3.6 KB written); None once the kernel changes
-DRAM_BYTES_PER_SHOT = (7.370e6 + 3.58e3) / 100000
+# DRAM bytes per shot of the BP kernel from one ncu capture of a 100k-shot
+# launch of the current build; None until that capture is taken, and again
+# once the kernel changes
+DRAM_BYTES_PER_SHOT = None
 WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
 
 
@@ -71,6 +72,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="bb144: skip the mixed-batch and length-882 legs reported beside the headline")
     ap.add_argument("--train-steps", type=int, default=100, help="learned: training steps")
     ap.add_argument("--train-batch", type=int, default=512, help="learned: shots per training step")
     return ap.parse_args()
@@ -134,9 +137,9 @@ class ClockSampler:
                 "reasons": seen, "samples": len(rows)}
 
 
-def cpu_baseline(seconds: float):
-    """The oracle (FP64, as it stands) on host cores: shots/s of the same
-    workload on a bounded sample (shots taken round-robin over p)."""
+def _oracle_rate(seconds: float, threads: int, precision: str):
+    """Shots/s of the oracle (as it stands) on `threads` host threads over a
+    bounded sample of the workload (shots taken round-robin over p)."""
     import concurrent.futures as cf
 
     import oracle
@@ -144,7 +147,6 @@ def cpu_baseline(seconds: float):
 
     code = named_code(CODE)
     n = code.n
-    cores = os.cpu_count() or 1
     sets = {"HZ": oracle.collect_subtrees(code.HZ, R, SEED), "HX": oracle.collect_subtrees(code.HX, R, SEED + 1)}
     chunk = 4
 
@@ -156,16 +158,16 @@ def cpu_baseline(seconds: float):
         llr = np.full(n, np.log((1 - pm) / pm))
         for H, e, key in ((code.HZ, ex, "HZ"), (code.HX, ez, "HX")):
             s = oracle.syndrome(H, e)
-            oracle.mbbp_decode(H, sets[key], s, llr, ITERS, ALPHA, precision="f64")
+            oracle.mbbp_decode(H, sets[key], s, llr, ITERS, ALPHA, precision=precision)
         return chunk
 
     done = 0
     t0 = time.perf_counter()
     k = 0
-    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
         futs = set()
         while time.perf_counter() - t0 < seconds or futs:
-            while len(futs) < cores and time.perf_counter() - t0 < seconds:
+            while len(futs) < threads and time.perf_counter() - t0 < seconds:
                 futs.add(ex.submit(work, k))
                 k += 1
             finished, futs = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
@@ -173,9 +175,25 @@ def cpu_baseline(seconds: float):
     dt = time.perf_counter() - t0
     # every chunk covers one p; the workload mixes the four p equally, which the
     # round-robin order reproduces up to the last partial round
-    return {"value": done / dt, "unit": "shots/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} depolarizing shots of the workload (X and Z decoded, p round-robin over "
-                      f"{list(P_LIST)}), oracle FP64, {cores} threads, {dt:.1f} s"}
+    return done / dt, done, dt
+
+
+def cpu_baseline(seconds: float, extra_modes: bool = True):
+    """The oracle (as it stands) on the host cores: FP64 on every core (the
+    reported value), and beside it FP64 on one core and the FP32 oracle on
+    every core."""
+    cores = os.cpu_count() or 1
+    v, done, dt = _oracle_rate(seconds, cores, "f64")
+    out = {"value": v, "unit": "shots/s", "cores": cores, "kind": "oracle",
+           "sample": f"{done} depolarizing shots of the workload (X and Z decoded, p round-robin over "
+                     f"{list(P_LIST)}), oracle FP64, {cores} threads (nproc {cores}), {dt:.1f} s"}
+    if extra_modes:
+        v1, d1, t1 = _oracle_rate(seconds / 3, 1, "f64")
+        v32, d32, t32 = _oracle_rate(seconds / 3, cores, "f32")
+        out["fp64_one_core"] = {"value": v1, "unit": "shots/s", "cores": 1, "sample": f"{d1} shots, {t1:.1f} s"}
+        out["fp32_all_cores"] = {"value": v32, "unit": "shots/s", "cores": cores,
+                                 "sample": f"{d32} shots, {t32:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -184,13 +202,13 @@ def run_reference(args):
         return
     budget = max(2.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
-        cpu_baseline(budget / 4)
+        cpu_baseline(budget / 4, extra_modes=False)
     vals, t_all = [], time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(budget)["value"])
+        vals.append(cpu_baseline(budget, extra_modes=False)["value"])
     total = time.perf_counter() - t_all
     value = statistics.mean(vals)
-    cb = cpu_baseline(budget)
+    cb = cpu_baseline(budget, extra_modes=False)
     line = {
         "impl": "reference", "metric": "decoded shots/s", "value": value, "unit": "shots/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -208,13 +226,12 @@ MIXED = (("bb72", 8), ("bb144", 16), ("bb288", 32))
 MIXED_P = 0.05
 
 
-def run_mixed(args):
+def mixed_measure(shots: int, steps: int, warmup: int, sample_clocks: bool = False):
     """[[72]], [[144]] and [[288]] shots 1:1:1 (R = 8 / 16 / 32), depolarizing
     p = 0.05, X and Z decoded: one autotuned, graph-captured mbbp_decode_mixed
     per step (a persistent launch per kernel body and small-code shape)
-    against one plain
-    mbbp_decode per (code, type) on the same syndromes (identical outputs,
-    hence identical LER)."""
+    against one plain mbbp_decode per (code, type) on the same syndromes
+    (identical outputs, hence identical LER).  Returns the measurements."""
     import torch
 
     from paper_2605_14170_gb300 import mbbp
@@ -222,11 +239,11 @@ def run_mixed(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    per_code = max(1, args.shots // 3)
+    per_code = max(1, shots // 3)
     entries = []  # (code, bases for X errors / Z errors, logicals)
-    for name, R in MIXED:
+    for name, R_ in MIXED:
         c = named_code(name)
-        entries.append((c, mbbp.mbbp_build_bases(c.HZ, R, SEED), mbbp.mbbp_build_bases(c.HX, R, SEED + 1),
+        entries.append((c, mbbp.mbbp_build_bases(c.HZ, R_, SEED), mbbp.mbbp_build_bases(c.HX, R_, SEED + 1),
                         mbbp.mbbp_logicals_build(c.HZ, c.HX), mbbp.mbbp_logicals_build(c.HX, c.HZ)))
     bases = [b for e in entries for b in (e[1], e[2])]
     P = mbbp.mbbp_plan_create(bases)
@@ -265,71 +282,156 @@ def run_mixed(args):
     plain_out = [mbbp.decode(B, s, l, ITERS, ALPHA) for B, s, l in zip(bases, synd, llrs)]
     counts = torch.zeros((len(bases), 3), dtype=torch.int64, device=dev)
     launches = {"mixed": 0, "plain": 0}
+    kinds = mbbp.mbbp_plan_info(P)["kind"]
+    small = {entries[j // 2][0].name for j, k in enumerate(kinds) if k == 0}
+    bp_launches = len(small) + (1 if any(k == 1 for k in kinds) else 0)
+    dec_ms = {"mixed": [], "plain": []}
 
-    def step_mixed(k):
+    def step_mixed(k, record):
         sample(k)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
         graph.replay()
+        if record:
+            e1.record()
+            dec_ms["mixed"].append((e0, e1))
         for i, (_, _, _, LZ, LX) in enumerate(entries):
             mbbp.mbbp_judge(LZ, errs[i][0], ios[2 * i]["e_hat"], None, counts[2 * i])
             mbbp.mbbp_judge(LX, errs[i][1], ios[2 * i + 1]["e_hat"], None, counts[2 * i + 1])
         # sample+syndrome, BP (the generic launch and one per small-code shape;
         # each code here has its own shape), FWS per entry, judge
-        kinds = mbbp.mbbp_plan_info(P)["kind"]
-        small = {entries[j // 2][0].name for j, k in enumerate(kinds) if k == 0}
-        bp = len(small) + (1 if any(k == 1 for k in kinds) else 0)
-        launches["mixed"] = 9 + bp + len(bases) + 6
+        launches["mixed"] = 9 + bp_launches + len(bases) + 6
 
-    def step_plain(k):
+    def step_plain(k, record):
         sample(k)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
         for j, (B, s, l) in enumerate(zip(bases, synd, llrs)):
             o = plain_out[j]
             mbbp.mbbp_decode(B, s, l, ITERS, ALPHA, mbbp.RULE_NMS, o["e_hat"], o["conv"], o["success"],
                              o["workspace"], iters_run=o["iters"], selected=o["selected"])
+        if record:
+            e1.record()
+            dec_ms["plain"].append((e0, e1))
         launches["plain"] = 9 + 2 * len(bases)
 
     def timed(fn):
-        for k in range(args.warmup):
-            fn(k)
+        for k in range(warmup):
+            fn(k, False)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for k in range(args.steps):
-            fn(args.warmup + k)
+        for k in range(steps):
+            fn(warmup + k, True)
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    with ClockSampler(0) as clk:
-        ms_mixed = timed(step_mixed)
+    clk = ClockSampler(0) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    ms_mixed = timed(step_mixed)
+    if clk:
+        clk.__exit__(None, None, None)
     counts_mixed = counts.clone()
     ms_plain = timed(step_plain)
     # identical outputs on the last step's syndromes
     same = all(torch.equal(x["e_hat"], o["e_hat"]) and torch.equal(x["iters"], o["iters"])
                for x, o in zip(ios, plain_out))
-    shots = args.steps * 3 * per_code
+    n_shots = steps * 3 * per_code
     info = mbbp.mbbp_plan_info(P)
     cnt = counts_mixed.cpu().numpy()
     names = [f"{c.name}:{t}" for c, *_ in entries for t in ("X", "Z")]
-    line = {
-        "metric": "decoded shots/s", "value": shots / (ms_mixed / 1e3), "unit": "shots/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "mixed batch: [[72,12,6]] R=8, [[144,12,12]] R=16, [[288,12,18]] R=32, "
-                               "1:1:1, depolarizing p=0.05, X and Z decoded, 100 iters, persistent autotuned "
-                               "launches (one per kernel body and small-code shape) replayed as one CUDA graph",
-                   "shots_per_step": 3 * per_code,
-                   "alpha": ALPHA},
-        "plain": {"value": shots / (ms_plain / 1e3), "unit": "shots/s", "ms_per_step": ms_plain / args.steps,
-                  "launches_per_step": launches["plain"]},
-        "speedup_vs_plain": ms_plain / ms_mixed,
+    dm = statistics.mean(a.elapsed_time(b) for a, b in dec_ms["mixed"])
+    dp = statistics.mean(a.elapsed_time(b) for a, b in dec_ms["plain"])
+    return {
+        "shots_per_step": 3 * per_code, "steps": steps, "warmup": warmup,
+        "value": n_shots / (ms_mixed / 1e3), "unit": "shots/s", "ms_per_step": ms_mixed / steps,
+        "decode_ms": dm,
+        "plain": {"value": n_shots / (ms_plain / 1e3), "unit": "shots/s", "ms_per_step": ms_plain / steps,
+                  "decode_ms": dp, "launches_per_step": launches["plain"]},
+        "speedup_vs_plain": ms_plain / ms_mixed, "decode_speedup_vs_plain": dp / dm,
         "outputs_identical_to_plain": bool(same),
-        "ler": {nm: float(cnt[j, 1] + cnt[j, 2]) / (args.steps * per_code) for j, nm in enumerate(names)},
+        "ler": {nm: float(cnt[j, 1] + cnt[j, 2]) / (steps * per_code) for j, nm in enumerate(names)},
         "plan": {"warps": info["warps"], "chunk": info["chunk"], "kind": info["kind"], "order": info["order"],
                  "autotuned_ms": tuned_ms},
-        "gpu_launches": launches["mixed"] * args.steps,
-        "clocks": clk.summary(),
+        "launches_per_step": launches["mixed"],
+        "clocks": clk.summary() if clk else None,
+    }
+
+
+MIXED_WORKLOAD = ("mixed batch: [[72,12,6]] R=8, [[144,12,12]] R=16, [[288,12,18]] R=32, 1:1:1, depolarizing "
+                  "p=0.05, X and Z decoded, 100 iters, persistent autotuned launches (one per kernel body and "
+                  "small-code shape) replayed as one CUDA graph")
+
+
+def run_mixed(args):
+    """The mixed-batch workload as its own JSON line."""
+    r = mixed_measure(args.shots, args.steps, args.warmup, sample_clocks=True)
+    line = {
+        "metric": "decoded shots/s", "value": r["value"], "unit": "shots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": MIXED_WORKLOAD, "shots_per_step": r["shots_per_step"], "alpha": ALPHA},
+        "plain": r["plain"], "speedup_vs_plain": r["speedup_vs_plain"],
+        "decode_speedup_vs_plain": r["decode_speedup_vs_plain"],
+        "outputs_identical_to_plain": r["outputs_identical_to_plain"], "ler": r["ler"], "plan": r["plan"],
+        "gpu_launches": r["launches_per_step"] * args.steps, "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
+
+
+GB882_P = (0.02, 0.03, 0.04, 0.05, 0.06)
+
+
+def gb882_measure(shots: int, steps: int = 1, warmup: int = 1):
+    """Plain MBBP-LD on the length-882 GB code (R = 64, 100 iterations,
+    depolarizing p in {0.02 .. 0.06}, X errors decoded with H_Z): shots/s per
+    p from CUDA events around each decode call (BP + FWS), inputs resident."""
+    import torch
+
+    from paper_2605_14170_gb300 import mbbp
+    from paper_2605_14170_gb300.inputs import named_code
+
+    dev = torch.device("cuda", 0)
+    c = named_code("gb882")
+    n, W = c.n, (c.n + 31) // 32
+    t0 = time.perf_counter()
+    B = mbbp.mbbp_build_bases(c.HZ, 64, SEED)
+    build_s = time.perf_counter() - t0
+    ex = torch.empty((shots, W), dtype=torch.int32, device=dev)
+    ez = torch.empty_like(ex)
+    syn = torch.empty((shots, B.m), dtype=torch.uint8, device=dev)
+    out = None
+    per_p = {}
+    for ip, p in enumerate(GB882_P):
+        mbbp.mbbp_sample_errors(n, shots, 90_000_000_000 + ip * shots, SEED, p, mbbp.NOISE_DEPOLARIZING, ex, ez)
+        mbbp.mbbp_syndrome(B, ex, syn)
+        pm = 2 * p / 3
+        llr = torch.full((n,), float(np.log((1 - pm) / pm)), dtype=torch.float32, device=dev)
+        if out is None:
+            out = mbbp.decode(B, syn, llr, ITERS, ALPHA)
+        times = []
+        for k in range(warmup + steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mbbp.mbbp_decode(B, syn, llr, ITERS, ALPHA, mbbp.RULE_NMS, out["e_hat"], out["conv"], out["success"],
+                             out["workspace"], iters_run=out["iters"], selected=out["selected"])
+            e1.record()
+            e1.synchronize()
+            if k >= warmup:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.mean(times)
+        it = (out["iters"].to(torch.int64) & 0xFFFF).float().mean().item()
+        per_p[str(p)] = {"shots_per_s": shots / (ms / 1e3), "decode_ms": ms, "mean_K": it,
+                         "success": float(out["success"].float().mean().item())}
+    total_ms = sum(v["decode_ms"] for v in per_p.values())
+    return {"workload": "length-882 GB code (seeded, k=4), R=64, 100 iters, alpha 0.625, flooding, FWS, "
+                        "depolarizing X errors", "shots_per_p": shots, "steps": steps, "warmup": warmup,
+            "shots_per_s": len(GB882_P) * shots / (total_ms / 1e3), "per_p": per_p,
+            "bases_build_s": build_s}
 
 
 def run_learned(args):
@@ -754,6 +856,15 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(args, mbbp, BZ, BX, llrs, S, dev, stream, rank, world)
 
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        # the other two decode configurations, measured on the same GPU after
+        # the headline's timed region: the mixed batch (3e5 shots, graph-
+        # replayed persistent launches vs per-code launches) and plain
+        # MBBP-LD on the length-882 GB code with R = 64
+        extra = {"mixed": mixed_measure(300_000, 5, 3), "gb882_r64_plain": gb882_measure(100_000)}
+        extra["mixed"]["workload"] = MIXED_WORKLOAD
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(args.cpu_seconds)
@@ -782,26 +893,31 @@ def main():
                                     "mean_K_max_per_shot": float(ks[i, 1]) / (2 * args.steps * S * world)}
                            for i, p in enumerate(P_LIST)},
             "ler": ler,
-            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s", "frac": achieved_ops / peak_ops,
-                         "traffic": DRAM_BYTES_PER_SHOT * S,
+            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops_128 / 1e12,
+                         "unit": "Tops/s", "frac": achieved_ops / peak_ops_128,
+                         "traffic": DRAM_BYTES_PER_SHOT * S if DRAM_BYTES_PER_SHOT is not None else None,
                          "traffic_note": "dram read+write of the BP kernel from one ncu capture of a "
                                          "100k-shot launch (profiles/decode_small_kernel_bb144_r16.md), "
                                          "scaled by shots",
                          "kernel": "mbbp_decode (BP + FWS)", "decode_ms_avg": dec_avg_ms,
                          "edge_updates_per_launch": edge_per_launch,
                          "ops_per_edge_update": OPS_PER_EDGE_UPDATE,
-                         "peak_basis": f"{sm_count} SMs x {peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max "
-                                       f"SM clock) x {OPS_PER_EDGE_UPDATE} ops x min({ALU_LANES}/{ALU_OPS} alu, "
-                                       f"{FMA_LANES}/{FMA_OPS} fma, {ISSUE_LANES}/{OPS_PER_EDGE_UPDATE} issue) "
-                                       "edge-updates per SM per clock; pipe widths confirmed by the probes",
-                         "peak_128_lanes": peak_ops_128 / 1e12, "frac_128_lanes": achieved_ops / peak_ops_128,
+                         "peak_basis": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                       f"({peak_kind} max SM clock): every algorithmic operation at one lane-issue",
+                         "peak_op_mix": peak_ops / 1e12, "frac_op_mix": achieved_ops / peak_ops,
+                         "peak_op_mix_basis": f"{sm_count} SMs x {peaks.get('sm_max_mhz', 2070.0)} MHz x "
+                                              f"{OPS_PER_EDGE_UPDATE} ops x min({ALU_LANES}/{ALU_OPS} alu, "
+                                              f"{FMA_LANES}/{FMA_OPS} fma, {ISSUE_LANES}/{OPS_PER_EDGE_UPDATE} "
+                                              "issue) edge-updates per SM per clock; pipe widths confirmed by "
+                                              "the probes",
                          "probe": probe},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
         if e2e is not None:
             line["e2e"] = e2e
+        if extra is not None:
+            line["extra"] = extra
         if cb is not None:
             line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)

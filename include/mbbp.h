@@ -254,6 +254,23 @@ mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndro
                            uint8_t* success, int16_t* selected, float* posterior,
                            void* workspace, size_t workspace_bytes, void* stream);
 
+/* mbbp_decode_ex (flooding schedule only) that also records the messages
+ * behind the posteriors: for every (shot, representation), the check-to-
+ * variable messages m_{c->v} of Eq. (2) of the last iteration it ran.
+ * c2v: device float[batch*R*E], E = the largest edge count of the
+ * representations (mbbp_bases_info); entry e of (shot, t) is edge e of H^(t)
+ * with edges numbered row by row, columns ascending (the numbering of the
+ * WMS weights).  Entries past the representation's own edge count, and all
+ * entries of an item that stopped at K = 0, are left as they were.  For
+ * tests and debugging (comparison with a reference decoder); the trace
+ * costs one extra global store per message and iteration.  MBBP_E_INVALID
+ * for the serial schedule or a NULL c2v. */
+mbbp_status mbbp_decode_trace(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                              const float* llr, int llr_stride, int iters, const mbbp_options* opt,
+                              uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run,
+                              uint8_t* success, int16_t* selected, float* posterior, float* c2v,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * Mixed batches: several codes decoded by persistent launches.
  * ---------------------------------------------------------------------- */

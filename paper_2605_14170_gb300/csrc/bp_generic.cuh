@@ -109,14 +109,21 @@ __device__ __forceinline__ void check_out(const float (&q)[DC], float* msg, int 
     }
 }
 
-// Flooding check pass of row r: its q messages are in its own slots.
+// Flooding check pass of row r: its q messages are in its own slots.  With
+// a trace pointer tr, the row's new messages also go to tr[0..deg) (edge j of
+// the row is its j-th column in ascending order).
 template <int DC, int RULE>
 __device__ __forceinline__ void check_row(float* msg, int r, int MP, int deg, uint32_t sbit,
-                                          float alpha) {
+                                          float alpha, float* tr = nullptr) {
     float q[DC];
 #pragma unroll
     for (int j = 0; j < DC; ++j) q[j] = (j < deg) ? msg[j * MP + r] : MBBP_LMAX;
     check_out<DC, RULE>(q, msg, r, MP, deg, sbit, alpha);
+    if (tr) {
+#pragma unroll
+        for (int j = 0; j < DC; ++j)
+            if (j < deg) tr[j] = msg[j * MP + r];
+    }
 }
 
 // Variable-node update of a degree-D variable (Eq. (3)): q_i = mu + sum of
@@ -184,8 +191,9 @@ __device__ __forceinline__ void store_item(const ShotIO& io, unsigned long long 
 
 // Decode one (shot, representation) item.  area: this warp's shared-memory
 // area (warp_layout(DC, ...).per_warp bytes); hcol: columns of the rows of H
-// ([DC][mpad], shared or global memory).
-template <int DC, int DV, int RULE>
+// ([DC][mpad], shared or global memory).  TRACE: io.c2v receives the check
+// messages of every iteration (the last one run remains).
+template <int DC, int DV, int RULE, bool TRACE = false>
 __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, int shot, int b,
                                          unsigned char* area, const uint16_t* hcol) {
     const int lane = threadIdx.x & 31;
@@ -261,7 +269,10 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
             const int r = lane + 32 * k;
             if (r < Mb) {
                 const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
-                check_row<DC, RULE>(msg, r, MP, deg, (sb >> k) & 1u, io.alpha);
+                float* tr = TRACE ? io.c2v + item * (unsigned long long)io.c2v_stride +
+                                        __ldg(B.rowptr + (size_t)b * MP + r)
+                                  : nullptr;
+                check_row<DC, RULE>(msg, r, MP, deg, (sb >> k) & 1u, io.alpha, tr);
             }
         }
         __syncwarp();

@@ -48,10 +48,14 @@ __device__ __forceinline__ void sts(char* smc, uint32_t off, float v) {
 
 // Check update of one row (one row per lane) whose messages q[] were loaded
 // from byte offsets cb[j] + 128 k: Eq. (2) with the syndrome sign, or the
-// sum-product rule through Gallager's phi.
-template <int K, int RULE, bool REG>
+// sum-product rule through Gallager's phi.  TRACE also writes every message
+// to tr[edge id], the edge id of slot j * MP + ((lane + rot(j)) & 31) + 32 k
+// coming from se (the representation's slot-to-edge table).
+template <int K, int RULE, bool REG, bool TRACE>
 __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const uint32_t (&cb)[K],
-                                          int k, int deg, bool valid, uint32_t sbit, float alpha) {
+                                          int k, int deg, bool valid, uint32_t sbit, float alpha,
+                                          float* tr, const int32_t* se, int MP) {
+    const int lane = threadIdx.x & 31;
     uint32_t sx = sbit << 31;
 #pragma unroll
     for (int j = 0; j < K; ++j) sx ^= __float_as_uint(q[j]);
@@ -71,7 +75,10 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
             const float excl = (j == K - 1) ? pre[j] : (j == 0 ? fminf(MBBP_LMAX, suf[0]) : fminf(pre[j], suf[j]));
             const uint32_t mag = __float_as_uint(__fmul_rn(alpha, excl));
             const uint32_t out = mag ^ ((sx ^ __float_as_uint(q[j])) & 0x80000000u);
-            if (valid && (REG || j < deg)) sts(smc, cb[j] + 128 * k, __uint_as_float(out));
+            if (valid && (REG || j < deg)) {
+                sts(smc, cb[j] + 128 * k, __uint_as_float(out));
+                if (TRACE) tr[__ldg(se + j * MP + ((lane + slot_rot(j)) & 31) + 32 * k)] = __uint_as_float(out);
+            }
         }
     } else {
         float f[K];
@@ -86,7 +93,10 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
                 if (REG || t < deg) sum = __fadd_rn(sum, f[t]);
             const float mag = fminf(phi(sum), MBBP_SP_MAX);
             const uint32_t out = (__float_as_uint(mag) ^ sx) ^ (__float_as_uint(q[j]) & 0x80000000u);
-            if (valid && (REG || j < deg)) sts(smc, cb[j] + 128 * k, __uint_as_float(out));
+            if (valid && (REG || j < deg)) {
+                sts(smc, cb[j] + 128 * k, __uint_as_float(out));
+                if (TRACE) tr[__ldg(se + j * MP + ((lane + slot_rot(j)) & 31) + 32 * k)] = __uint_as_float(out);
+            }
             pre = __fadd_rn(pre, f[j]);
         }
     }
@@ -134,7 +144,9 @@ __device__ __forceinline__ float var_step(char* smc, int deg, const uint4& d, fl
 
 // Decode shots [shot_begin, shot_end) on representation b.  smc is the
 // dynamic shared array, wbase the byte offset of this warp's area in it.
-template <int VS, int RS, int ORS, int RULE, bool REG>
+// TRACE: io.c2v receives the check messages of every iteration (the last
+// one run remains).
+template <int VS, int RS, int ORS, int RULE, bool REG, bool TRACE = false>
 __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, int b, int shot_begin,
                                           int shot_end, char* smc, uint32_t wbase) {
     constexpr int K = 6;
@@ -185,6 +197,7 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
         const unsigned long long item = (unsigned long long)shot * R + b;
         const float* llr = io.llr + (size_t)shot * io.llr_stride;
         const uint8_t* sy = io.synd + (size_t)shot * m;
+        float* tr = TRACE ? io.c2v + item * (unsigned long long)io.c2v_stride : nullptr;
         float mu[VS];
         uint32_t ew[VS];
 #pragma unroll
@@ -266,7 +279,8 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
                 if (32 * k < Mb) {
                     const bool valid = lane + 32 * k < Mb;
                     const int deg = REG ? K : (int)((rowdeg >> (4 * k)) & 0xfu);
-                    check_row<K, RULE, REG>(smc, q[k], cb, k, deg, valid, (sb >> k) & 1u, io.alpha);
+                    check_row<K, RULE, REG, TRACE>(smc, q[k], cb, k, deg, valid, (sb >> k) & 1u, io.alpha, tr,
+                                                   B.sedge + (size_t)b * K * MP, MP);
                 }
             }
             __syncwarp();

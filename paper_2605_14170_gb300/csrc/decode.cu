@@ -29,7 +29,7 @@ void* g_scratch_addr[kMaxDevices] = {};
 // several small ones.  Each class is compiled for its own block size.
 constexpr int kGenericWideWarps = 16;
 
-template <int DC, int DV, int RULE, int MAXW>
+template <int DC, int DV, int RULE, int MAXW, bool TRACE = false>
 __global__ void __launch_bounds__(MAXW * 32)
 decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -49,7 +49,7 @@ decode_kernel(const DecodeArgs a) {
         if (item >= a.total_items) break;
         const int shot = (int)(item / (unsigned long long)R);
         const int b = (int)(item - (unsigned long long)shot * R);
-        generic_bp::run_item<DC, DV, RULE>(B, a.io, shot, b, area, hcol_s);
+        generic_bp::run_item<DC, DV, RULE, TRACE>(B, a.io, shot, b, area, hcol_s);
     }
 }
 
@@ -216,10 +216,10 @@ cudaError_t launch_serial_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
     return cudaGetLastError();
 }
 
-template <int K, int RULE>
+template <int K, int RULE, bool TRACE>
 cudaError_t launch_decode_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
-    const void* narrow = reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock>);
-    const void* wide = reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps>);
+    const void* narrow = reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE>);
+    const void* wide = reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps, TRACE>);
     const generic_bp::WarpLayout L = generic_bp::warp_layout(K, a.B.MP, a.B.mpad, a.B.n);
     // per class, the block size with the most resident warps per SM (ties:
     // the smaller block) within 200 KB of shared memory per block; the wide
@@ -246,10 +246,15 @@ cudaError_t launch_decode_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
     unsigned long long grid = (unsigned long long)per_sm * (unsigned long long)sm_count;
     if (want < grid) grid = want;
     if (use_wide)
-        decode_kernel<K, K, RULE, kGenericWideWarps><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+        decode_kernel<K, K, RULE, kGenericWideWarps, TRACE><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     else
-        decode_kernel<K, K, RULE, kWarpsPerBlock><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+        decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int K, int RULE>
+cudaError_t launch_decode_k(const DecodeArgs& a, cudaStream_t s, int sm_count) {
+    return a.io.c2v ? launch_decode_t<K, RULE, true>(a, s, sm_count) : launch_decode_t<K, RULE, false>(a, s, sm_count);
 }
 
 }  // namespace
@@ -311,13 +316,13 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s, int sm_count) {
     if (a.B.shape != 0) return launch_decode_small(a, s, sm_count);
     const int K = a.B.DC;
     if (a.rule == MBBP_RULE_NMS) {
-        if (K == 6) return launch_decode_t<6, MBBP_RULE_NMS>(a, s, sm_count);
-        if (K == 8) return launch_decode_t<8, MBBP_RULE_NMS>(a, s, sm_count);
-        if (K == 12) return launch_decode_t<12, MBBP_RULE_NMS>(a, s, sm_count);
+        if (K == 6) return launch_decode_k<6, MBBP_RULE_NMS>(a, s, sm_count);
+        if (K == 8) return launch_decode_k<8, MBBP_RULE_NMS>(a, s, sm_count);
+        if (K == 12) return launch_decode_k<12, MBBP_RULE_NMS>(a, s, sm_count);
     } else {
-        if (K == 6) return launch_decode_t<6, MBBP_RULE_SP>(a, s, sm_count);
-        if (K == 8) return launch_decode_t<8, MBBP_RULE_SP>(a, s, sm_count);
-        if (K == 12) return launch_decode_t<12, MBBP_RULE_SP>(a, s, sm_count);
+        if (K == 6) return launch_decode_k<6, MBBP_RULE_SP>(a, s, sm_count);
+        if (K == 8) return launch_decode_k<8, MBBP_RULE_SP>(a, s, sm_count);
+        if (K == 12) return launch_decode_k<12, MBBP_RULE_SP>(a, s, sm_count);
     }
     return cudaErrorInvalidValue;
 }

@@ -625,6 +625,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
                 shape = i + 1;
     std::vector<uint4> vdesc2;
     std::vector<uint32_t> rinfo2, hmask2;
+    std::vector<int32_t> sedge;  // [R][6*MP] edge id (row by row, columns ascending) of every slot, or -1
     int VS = 0, RS = 0, ORS = 0;
     if (shape) {
         VS = kSmallShapes[shape - 1].VS;
@@ -633,6 +634,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         vdesc2.assign((size_t)R * VS * 32, make_uint4(0, 0, 0, 0));
         rinfo2.assign((size_t)R * MP, 0);
         hmask2.assign((size_t)R * VS * ORS * 32, 0);
+        sedge.assign((size_t)R * 6 * MP, -1);
         for (int t = 0; t < R; ++t) {
             const int extra = set_ptr[t + 1] - set_ptr[t];
             std::vector<int> src(m + extra);
@@ -647,7 +649,9 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
                 rinfo2[(size_t)t * MP + sg] = (uint32_t)src[r] | ((uint32_t)cols.size() << 16);
                 for (int j = 0; j < (int)cols.size(); ++j) {
                     const int sj = L.slot[r][j];
-                    vs[cols[j]].push_back((uint16_t)(sj * MP + (sg & ~31) + ((sg + slot_rot(sj)) & 31)));
+                    const int sl = sj * MP + (sg & ~31) + ((sg + slot_rot(sj)) & 31);
+                    vs[cols[j]].push_back((uint16_t)sl);
+                    sedge[(size_t)t * 6 * MP + sl] = rowptr[(size_t)t * MP + r] + j;
                 }
             }
             // byte offsets within a warp's message area; a missing edge (and
@@ -706,7 +710,8 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     const size_t o_vdesc3 = o_edesc + align256(edesc.size() * sizeof(uint4));
     const size_t o_lpos = o_vdesc3 + align256(vdesc3.size() * sizeof(uint4));
     const size_t o_rinfo_s = o_lpos + align256(lpos.size() * 2);
-    const size_t total = o_rinfo_s + align256(rinfo_s.size() * 4);
+    const size_t o_sedge = o_rinfo_s + align256(rinfo_s.size() * 4);
+    const size_t total = o_sedge + align256(sedge.size() * 4);
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
     if (e == cudaSuccess) e = cudaMalloc(&B->dmem, total);
@@ -734,6 +739,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         {o_vdesc3, vdesc3.data(), vdesc3.size() * sizeof(uint4)},
         {o_lpos, lpos.data(), lpos.size() * 2},
         {o_rinfo_s, rinfo_s.data(), rinfo_s.size() * 4},
+        {o_sedge, sedge.data(), sedge.size() * 4},
     };
     for (const Copy& c : copies) {
         if (c.bytes == 0) continue;
@@ -761,6 +767,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     d.vdesc2 = shape ? reinterpret_cast<const uint4*>(base + o_vdesc2) : nullptr;
     d.rinfo2 = shape ? reinterpret_cast<const uint32_t*>(base + o_rinfo2) : nullptr;
     d.hmask2 = shape ? reinterpret_cast<const uint32_t*>(base + o_hmask2) : nullptr;
+    d.sedge = shape ? reinterpret_cast<const int32_t*>(base + o_sedge) : nullptr;
     d.lrows = reinterpret_cast<const uint16_t*>(base + o_lrows);
     d.lptr = reinterpret_cast<const uint16_t*>(base + o_lptr);
     d.nlayers = reinterpret_cast<const int32_t*>(base + o_nlayers);
@@ -972,11 +979,15 @@ mbbp_status mbbp_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes
                           success, selected, posterior, workspace, workspace_bytes, stream);
 }
 
-mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndromes,
-                           const float* llr, int llr_stride, int iters, const mbbp_options* opt,
-                           uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,
-                           int16_t* selected, float* posterior, void* workspace,
-                           size_t workspace_bytes, void* stream) {
+namespace {
+
+// Argument checks of mbbp_decode_ex, before any CUDA call (the workspace
+// only when `need_ws`).  *launch = false when there is nothing to enqueue.
+mbbp_status decode_validate(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
+                            int llr_stride, int iters, const mbbp_options* opt, const uint8_t* e_hat,
+                            const uint8_t* conv, const uint8_t* success, bool need_ws, const void* workspace,
+                            size_t workspace_bytes, bool* launch) {
+    *launch = false;
     if (!B) return fail(MBBP_E_INVALID, "mbbp_decode: NULL handle");
     if (!opt) return fail(MBBP_E_INVALID, "mbbp_decode_ex: NULL options");
     const int rule = opt->rule;
@@ -992,13 +1003,35 @@ mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndro
         return fail(MBBP_E_INVALID, "alpha must be in (0, 1]");
     if (llr_stride != 0 && llr_stride < B->n) return fail(MBBP_E_INVALID, "llr_stride must be 0 or >= n");
     if (batch == 0) return MBBP_OK;
-    if (!syndromes || !llr || !e_hat || !conv || !success || !workspace)
+    if (!syndromes || !llr || !e_hat || !conv || !success)
         return fail(MBBP_E_INVALID, "mbbp_decode: NULL buffer");
-    if (workspace_bytes < mbbp_decode_workspace_size(B, batch))
-        return fail(MBBP_E_INVALID, "workspace too small");
-    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
-        return fail(MBBP_E_INVALID, "workspace must be 256-byte aligned");
+    if (need_ws) {
+        if (!workspace) return fail(MBBP_E_INVALID, "mbbp_decode: NULL buffer");
+        if (workspace_bytes < mbbp_decode_workspace_size(B, batch))
+            return fail(MBBP_E_INVALID, "workspace too small");
+        if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+            return fail(MBBP_E_INVALID, "workspace must be 256-byte aligned");
+    }
     if (mbbp_status st = check_device(B->device)) return st;
+    *launch = true;
+    return MBBP_OK;
+}
+
+}  // namespace
+
+namespace {
+
+mbbp_status decode_impl(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
+                        int llr_stride, int iters, const mbbp_options* opt, uint8_t* e_hat, uint8_t* conv,
+                        uint16_t* iters_run, uint8_t* success, int16_t* selected, float* posterior,
+                        void* workspace, size_t workspace_bytes, float* c2v, void* stream) {
+    bool launch = false;
+    if (mbbp_status st = decode_validate(B, batch, syndromes, llr, llr_stride, iters, opt, e_hat, conv, success,
+                                         true, workspace, workspace_bytes, &launch))
+        return st;
+    if (!launch) return MBBP_OK;
+    const int rule = opt->rule;
+    const float alpha = opt->alpha;
     cudaStream_t s = (cudaStream_t)stream;
     DecodeArgs a{};
     a.B = B->dev;
@@ -1015,6 +1048,8 @@ mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndro
     a.io.conv = conv;
     a.io.iters_run = iters_run;
     a.io.post = posterior;
+    a.io.c2v = c2v;
+    a.io.c2v_stride = *std::max_element(B->edges.begin(), B->edges.end());
     a.total_items = (unsigned long long)batch * B->R;
     a.rep_counter = reinterpret_cast<unsigned int*>(a.counter + 1);
     const size_t counter_bytes = sizeof(unsigned long long) + sizeof(unsigned int) * (size_t)B->R;
@@ -1040,13 +1075,47 @@ mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndro
     return e == cudaSuccess ? MBBP_OK : cuda_fail(e, "mbbp_decode (selection)");
 }
 
+}  // namespace
+
+mbbp_status mbbp_decode_ex(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                           const float* llr, int llr_stride, int iters, const mbbp_options* opt,
+                           uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,
+                           int16_t* selected, float* posterior, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+    return decode_impl(B, batch, syndromes, llr, llr_stride, iters, opt, e_hat, conv, iters_run, success,
+                       selected, posterior, workspace, workspace_bytes, nullptr, stream);
+}
+
+mbbp_status mbbp_decode_trace(const mbbp_bases* B, int batch, const uint8_t* syndromes,
+                              const float* llr, int llr_stride, int iters, const mbbp_options* opt,
+                              uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,
+                              int16_t* selected, float* posterior, float* c2v, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+    if (opt && opt->schedule != MBBP_SCHEDULE_FLOODING)
+        return fail(MBBP_E_INVALID, "mbbp_decode_trace: flooding schedule only");
+    if (!c2v && batch > 0) return fail(MBBP_E_INVALID, "mbbp_decode_trace: NULL c2v");
+    return decode_impl(B, batch, syndromes, llr, llr_stride, iters, opt, e_hat, conv, iters_run, success,
+                       selected, posterior, workspace, workspace_bytes, c2v, stream);
+}
+
 mbbp_status mbbp_decode_noalloc(const mbbp_bases* B, int batch, const uint8_t* syndromes,
                                 const float* llr, int llr_stride, int iters, float alpha, int rule,
                                 uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run,
                                 uint8_t* success, int16_t* selected, float* posterior,
                                 void* stream) {
     if (!B) return fail(MBBP_E_INVALID, "mbbp_decode_noalloc: NULL handle");
-    if (batch < 0) return fail(MBBP_E_INVALID, "batch must be >= 0");
+    mbbp_options o{};
+    o.rule = rule;
+    o.alpha = alpha;
+    o.schedule = MBBP_SCHEDULE_FLOODING;
+    o.decision = MBBP_DECISION_FWS;
+    // every argument is checked (and batch 0 returns) before the scratch
+    // address is looked up, so a call that launches nothing makes no CUDA call
+    bool launch = false;
+    if (mbbp_status st = decode_validate(B, batch, syndromes, llr, llr_stride, iters, &o, e_hat, conv, success,
+                                         false, nullptr, 0, &launch))
+        return st;
+    if (!launch) return MBBP_OK;
     const size_t need = mbbp_decode_workspace_size(B, batch);
     if (need > kStaticScratchBytes) {
         const size_t per_shot = (size_t)B->R * B->W * 4;

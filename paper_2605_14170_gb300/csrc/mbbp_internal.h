@@ -40,6 +40,7 @@ struct DevBases {
     const uint4* vdesc2;      // [R][VS*32] x = variable | degree << 16, y/z/w = 6 slot ids (u16)
     const uint32_t* rinfo2;   // [R][MP] ELL index -> src row | degree << 16
     const uint32_t* hmask2;   // [R][VS][ORS*32] rows of H as bit masks over positions
+    const int32_t* sedge;     // [R][6*MP] edge id of every message slot (-1: none), for message traces
     int shape, VS, RS, ORS;
 
     // Serial schedule: rows of H^(t) in layer order, layer boundaries and,
@@ -128,6 +129,8 @@ struct ShotIO {
     uint8_t* conv;            // [batch][R]
     uint16_t* iters_run;      // [batch][R] or null
     float* post;              // [batch][R][n] or null
+    float* c2v;               // [batch][R][c2v_stride] message trace (flooding kernels) or null
+    int c2v_stride;           // the largest edge count of the representations
 };
 
 struct DecodeArgs {

@@ -86,6 +86,8 @@ _sig = {
                               _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_decode_ex": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.POINTER(Options),
                                  _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "mbbp_decode_trace": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.POINTER(Options),
+                                    _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_decode_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
                                       _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mbbp_plan_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
@@ -145,10 +147,44 @@ def _dptr(t, dtype=None, name="buffer"):
     return C.c_void_p(t.data_ptr())
 
 
+def _out(t, dtype, name, numel, device):
+    """_dptr plus the checks the kernels rely on: at least `numel` elements
+    and the handle's device (an undersized or foreign buffer would be read or
+    written out of bounds)."""
+    if t is None:
+        return None
+    ptr = _dptr(t, dtype, name)
+    if t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements, got {t.numel()}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the handle on cuda:{device}")
+    return ptr
+
+
+def _llr_checked(llr, n, batch, device):
+    """Pointer and stride of a channel-LLR tensor: [n] (shared) or
+    [batch, stride >= n] (per shot)."""
+    import torch
+    if llr.dim() == 1:
+        return _out(llr, torch.float32, "llr", n, device), 0
+    stride = llr.shape[-1]
+    if stride < n:
+        raise ValueError(f"llr rows must hold at least n = {n} values, got {stride}")
+    return _out(llr, torch.float32, "llr", batch * stride, device), stride
+
+
 def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def _current_device():
+    try:
+        import torch
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except Exception:  # pragma: no cover
+        return None
 
 
 def mbbp_version() -> str:
@@ -199,6 +235,7 @@ class Bases:
         self.m, self.n, self.R = info["m"], info["n"], info["R"]
         self.rows, self.edges, self.sets = info["rows"], info["edges"], info["sets"]
         self.words = (self.n + 31) // 32
+        self.device = _current_device()  # the device its tables were copied to
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -275,8 +312,9 @@ def mbbp_sample_errors(n: int, batch: int, first_shot: int, seed: int, p: float,
                        ex, ez=None, stream=None) -> None:
     """ex / ez: int32 CUDA tensors of batch * ceil(n/32) words."""
     import torch
+    words = batch * ((n + 31) // 32)
     _check(_lib.mbbp_sample_errors(n, batch, first_shot, seed, float(p), noise,
-                                   _dptr(ex, torch.int32, "ex"), _dptr(ez, torch.int32, "ez"),
+                                   _out(ex, torch.int32, "ex", words, None), _out(ez, torch.int32, "ez", words, None),
                                    _stream(stream)), "mbbp_sample_errors")
 
 
@@ -284,12 +322,29 @@ def mbbp_syndrome(B: Bases, e, s, stream=None) -> None:
     """e: int32 [batch, W] packed errors; s: uint8 [batch, m]."""
     import torch
     batch = s.shape[0] if s.dim() > 1 else s.numel() // B.m
-    _check(_lib.mbbp_syndrome(B.handle, batch, _dptr(e, torch.int32, "e"),
-                              _dptr(s, torch.uint8, "s"), _stream(stream)), "mbbp_syndrome")
+    _check(_lib.mbbp_syndrome(B.handle, batch, _out(e, torch.int32, "e", batch * B.words, B.device),
+                              _out(s, torch.uint8, "s", batch * B.m, B.device), _stream(stream)), "mbbp_syndrome")
 
 
 def mbbp_decode_workspace_size(B: Bases, batch: int) -> int:
     return int(_lib.mbbp_decode_workspace_size(B.handle, batch))
+
+
+def _decode_io(B: Bases, syndromes, llr, e_hat, conv, success, iters_run, selected, posterior):
+    """Checked pointers of mbbp_decode's device arguments (shared by the
+    three decode entry points): batch, syndromes, llr, stride, then the
+    outputs in ABI order."""
+    import torch
+    batch = syndromes.shape[0]
+    if syndromes.numel() != batch * B.m:
+        raise ValueError("syndromes must be [batch, m]")
+    dev, n, R = B.device, B.n, B.R
+    llr_p, stride = _llr_checked(llr, n, batch, dev)
+    return (batch, _out(syndromes, torch.uint8, "syndromes", batch * B.m, dev), llr_p, stride,
+            _out(e_hat, torch.uint8, "e_hat", batch * n, dev), _out(conv, torch.uint8, "conv", batch * R, dev),
+            _out(iters_run, torch.int16, "iters_run", batch * R, dev),
+            _out(success, torch.uint8, "success", batch, dev), _out(selected, torch.int16, "selected", batch, dev),
+            _out(posterior, torch.float32, "posterior", batch * R * n, dev))
 
 
 def mbbp_decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int, e_hat, conv,
@@ -297,34 +352,39 @@ def mbbp_decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int, e
                 stream=None) -> None:
     """Algorithm 1 on a batch; see mbbp.h for every argument."""
     import torch
-    batch = syndromes.shape[0]
-    if syndromes.numel() != batch * B.m:
-        raise ValueError("syndromes must be [batch, m]")
-    stride = 0 if llr.dim() == 1 else llr.shape[-1]
+    batch, sp, lp, stride, ep, cp, ip, okp, selp, pp = _decode_io(B, syndromes, llr, e_hat, conv, success,
+                                                                  iters_run, selected, posterior)
     _check(_lib.mbbp_decode(
-        B.handle, batch, _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
-        stride, iters, float(alpha), rule, _dptr(e_hat, torch.uint8, "e_hat"),
-        _dptr(conv, torch.uint8, "conv"), _dptr(iters_run, torch.int16, "iters_run"),
-        _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
-        _dptr(posterior, torch.float32, "posterior"), _dptr(workspace, torch.uint8, "workspace"),
-        workspace.numel(), _stream(stream)), "mbbp_decode")
+        B.handle, batch, sp, lp, stride, iters, float(alpha), rule, ep, cp, ip, okp, selp, pp,
+        _out(workspace, torch.uint8, "workspace", 0, B.device), workspace.numel(), _stream(stream)),
+        "mbbp_decode")
 
 
 def mbbp_decode_ex(B: Bases, syndromes, llr, iters: int, opt: Options, e_hat, conv, success, workspace,
                    iters_run=None, selected=None, posterior=None, stream=None) -> None:
     """mbbp_decode with a schedule and a decision rule (Options)."""
     import torch
-    batch = syndromes.shape[0]
-    if syndromes.numel() != batch * B.m:
-        raise ValueError("syndromes must be [batch, m]")
-    stride = 0 if llr.dim() == 1 else llr.shape[-1]
+    batch, sp, lp, stride, ep, cp, ip, okp, selp, pp = _decode_io(B, syndromes, llr, e_hat, conv, success,
+                                                                  iters_run, selected, posterior)
     _check(_lib.mbbp_decode_ex(
-        B.handle, batch, _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
-        stride, iters, C.byref(opt), _dptr(e_hat, torch.uint8, "e_hat"),
-        _dptr(conv, torch.uint8, "conv"), _dptr(iters_run, torch.int16, "iters_run"),
-        _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
-        _dptr(posterior, torch.float32, "posterior"), _dptr(workspace, torch.uint8, "workspace"),
-        workspace.numel(), _stream(stream)), "mbbp_decode_ex")
+        B.handle, batch, sp, lp, stride, iters, C.byref(opt), ep, cp, ip, okp, selp, pp,
+        _out(workspace, torch.uint8, "workspace", 0, B.device), workspace.numel(), _stream(stream)),
+        "mbbp_decode_ex")
+
+
+def mbbp_decode_trace(B: Bases, syndromes, llr, iters: int, opt: Options, e_hat, conv, success, c2v, workspace,
+                      iters_run=None, selected=None, posterior=None, stream=None) -> None:
+    """mbbp_decode_ex (flooding) that also writes the last iteration's check
+    messages of every (shot, representation) to c2v, float32 [batch, R, E]
+    with E the largest edge count (edges row by row, columns ascending)."""
+    import torch
+    batch, sp, lp, stride, ep, cp, ip, okp, selp, pp = _decode_io(B, syndromes, llr, e_hat, conv, success,
+                                                                  iters_run, selected, posterior)
+    cvp = _out(c2v, torch.float32, "c2v", batch * B.R * int(B.edges.max()), B.device)
+    _check(_lib.mbbp_decode_trace(
+        B.handle, batch, sp, lp, stride, iters, C.byref(opt), ep, cp, ip, okp, selp, pp, cvp,
+        _out(workspace, torch.uint8, "workspace", 0, B.device), workspace.numel(), _stream(stream)),
+        "mbbp_decode_trace")
 
 
 def mbbp_decode_noalloc(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int, e_hat, conv,
@@ -332,17 +392,11 @@ def mbbp_decode_noalloc(B: Bases, syndromes, llr, iters: int, alpha: float, rule
     """mbbp_decode without a workspace, for callers that cannot allocate
     device memory: the scratch is the library's fixed array (see mbbp.h for
     its size limit and for why overlapping calls race)."""
-    import torch
-    batch = syndromes.shape[0]
-    if syndromes.numel() != batch * B.m:
-        raise ValueError("syndromes must be [batch, m]")
-    stride = 0 if llr.dim() == 1 else llr.shape[-1]
+    batch, sp, lp, stride, ep, cp, ip, okp, selp, pp = _decode_io(B, syndromes, llr, e_hat, conv, success,
+                                                                  iters_run, selected, posterior)
     _check(_lib.mbbp_decode_noalloc(
-        B.handle, batch, _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
-        stride, iters, float(alpha), rule, _dptr(e_hat, torch.uint8, "e_hat"),
-        _dptr(conv, torch.uint8, "conv"), _dptr(iters_run, torch.int16, "iters_run"),
-        _dptr(success, torch.uint8, "success"), _dptr(selected, torch.int16, "selected"),
-        _dptr(posterior, torch.float32, "posterior"), _stream(stream)), "mbbp_decode_noalloc")
+        B.handle, batch, sp, lp, stride, iters, float(alpha), rule, ep, cp, ip, okp, selp, pp,
+        _stream(stream)), "mbbp_decode_noalloc")
 
 
 class Plan:
@@ -379,16 +433,15 @@ def mbbp_plan_info(P: Plan) -> dict:
     return {"warps": warps.value, "chunk": chunk.tolist(), "kind": kind.tolist(), "order": order.tolist()}
 
 
-def _code_io(ios):
-    import torch
+def _code_io(P: Plan, ios):
+    if len(ios) != len(P.codes):
+        raise ValueError(f"the plan has {len(P.codes)} codes, got {len(ios)} inputs")
     arr = (CodeIO * len(ios))()
-    for i, x in enumerate(ios):
-        batch = x["syndromes"].shape[0]
-        llr = x["llr"]
-        arr[i] = CodeIO(batch, _dptr(x["syndromes"], torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
-                        0 if llr.dim() == 1 else llr.shape[-1], _dptr(x["e_hat"], torch.uint8, "e_hat"),
-                        _dptr(x["conv"], torch.uint8, "conv"), _dptr(x.get("iters"), torch.int16, "iters"),
-                        _dptr(x["success"], torch.uint8, "success"), _dptr(x.get("selected"), torch.int16, "selected"))
+    for i, (B, x) in enumerate(zip(P.codes, ios)):
+        batch, sp, lp, stride, ep, cp, ip, okp, selp, _ = _decode_io(
+            B, x["syndromes"], x["llr"], x["e_hat"], x["conv"], x["success"], x.get("iters"), x.get("selected"),
+            None)
+        arr[i] = CodeIO(batch, sp, lp, stride, ep, cp, ip, okp, selp)
     return arr
 
 
@@ -396,7 +449,7 @@ def mbbp_decode_mixed(P: Plan, ios, iters: int, alpha: float, rule: int, workspa
     """ios: one dict per code of the plan with CUDA tensors syndromes, llr,
     e_hat, conv, success and optionally iters (int16) and selected."""
     import torch
-    arr = _code_io(ios)
+    arr = _code_io(P, ios)
     _check(_lib.mbbp_decode_mixed(P.handle, arr, iters, float(alpha), rule,
                                   _dptr(workspace, torch.uint8, "workspace"), workspace.numel(), _stream(stream)),
            "mbbp_decode_mixed")
@@ -404,7 +457,7 @@ def mbbp_decode_mixed(P: Plan, ios, iters: int, alpha: float, rule: int, workspa
 
 def mbbp_plan_autotune(P: Plan, ios, iters: int, alpha: float, rule: int, workspace, stream=None) -> float:
     import torch
-    arr = _code_io(ios)
+    arr = _code_io(P, ios)
     best = C.c_float(0.0)
     _check(_lib.mbbp_plan_autotune(P.handle, arr, iters, float(alpha), rule,
                                    _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
@@ -446,48 +499,63 @@ def mbbp_wms_workspace_size(B: Bases, batch: int, T: int, ckpt: int) -> int:
     return int(_lib.mbbp_wms_workspace_size(B.handle, batch, T, ckpt))
 
 
-def _llr_stride(llr):
-    return 0 if llr.dim() == 1 else llr.shape[-1]
+def _wms_io(B, syndromes, llr, T, w, g, etrue):
+    """Checked pointers shared by the WMS entry points: batch, syndromes,
+    llr, stride, w, g, etrue."""
+    import torch
+    batch = syndromes.shape[0]
+    if syndromes.numel() != batch * B.m:
+        raise ValueError("syndromes must be [batch, m]")
+    dev = B.device
+    wn = B.R * T * int(B.edges.max())
+    llr_p, stride = _llr_checked(llr, B.n, batch, dev)
+    return (batch, _out(syndromes, torch.uint8, "syndromes", batch * B.m, dev), llr_p, stride,
+            _out(w, torch.float32, "w", wn, dev), _out(g, torch.float32, "g", wn, dev),
+            _out(etrue, torch.int32, "etrue", batch * B.words, dev))
 
 
 def mbbp_wms_forward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, posterior, loss, workspace,
                      all_iters=False, stream=None) -> None:
     import torch
+    batch, sp, lp, stride, wp, gp, ep = _wms_io(B, syndromes, llr, T, w, g, etrue)
+    dev = B.device
     _check(_lib.mbbp_wms_forward(
-        B.handle, syndromes.shape[0], _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
-        _llr_stride(llr), T, _dptr(w, torch.float32, "w"), _dptr(g, torch.float32, "g"), ckpt,
-        _dptr(etrue, torch.int32, "etrue"), float(scale), int(all_iters), _dptr(posterior, torch.float32, "posterior"),
-        _dptr(loss, torch.float32, "loss"), _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
-        _stream(stream)), "mbbp_wms_forward")
+        B.handle, batch, sp, lp, stride, T, wp, gp, ckpt, ep, float(scale), int(all_iters),
+        _out(posterior, torch.float32, "posterior", batch * B.R * B.n, dev),
+        _out(loss, torch.float32, "loss", batch * B.R, dev), _out(workspace, torch.uint8, "workspace", 0, dev),
+        workspace.numel(), _stream(stream)), "mbbp_wms_forward")
 
 
 def mbbp_wms_backward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, posterior, gw, gg, workspace,
                       all_iters=False, stream=None) -> None:
     import torch
+    batch, sp, lp, stride, wp, gp, ep = _wms_io(B, syndromes, llr, T, w, g, etrue)
+    dev = B.device
+    wn = B.R * T * int(B.edges.max())
     _check(_lib.mbbp_wms_backward(
-        B.handle, syndromes.shape[0], _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
-        _llr_stride(llr), T, _dptr(w, torch.float32, "w"), _dptr(g, torch.float32, "g"), ckpt,
-        _dptr(etrue, torch.int32, "etrue"), float(scale), int(all_iters), _dptr(posterior, torch.float32, "posterior"),
-        _dptr(gw, torch.float32, "gw"), _dptr(gg, torch.float32, "gg"), _dptr(workspace, torch.uint8, "workspace"),
-        workspace.numel(), _stream(stream)), "mbbp_wms_backward")
+        B.handle, batch, sp, lp, stride, T, wp, gp, ckpt, ep, float(scale), int(all_iters),
+        _out(posterior, torch.float32, "posterior", batch * B.R * B.n, dev),
+        _out(gw, torch.float32, "gw", wn, dev), _out(gg, torch.float32, "gg", wn, dev),
+        _out(workspace, torch.uint8, "workspace", 0, dev), workspace.numel(), _stream(stream)), "mbbp_wms_backward")
 
 
 def mbbp_wms_decode(B, syndromes, llr, iters, T, w, g, e_hat, conv, success, workspace, iters_run=None,
                     selected=None, stream=None) -> None:
     import torch
+    batch, sp, lp, stride, wp, gp, _ = _wms_io(B, syndromes, llr, T, w, g, None)
+    _, _, _, _, ep, cp, ip, okp, selp, _ = _decode_io(B, syndromes, llr, e_hat, conv, success, iters_run, selected,
+                                                      None)
     _check(_lib.mbbp_wms_decode(
-        B.handle, syndromes.shape[0], _dptr(syndromes, torch.uint8, "syndromes"), _dptr(llr, torch.float32, "llr"),
-        _llr_stride(llr), iters, T, _dptr(w, torch.float32, "w"), _dptr(g, torch.float32, "g"),
-        _dptr(e_hat, torch.uint8, "e_hat"), _dptr(conv, torch.uint8, "conv"),
-        _dptr(iters_run, torch.int16, "iters_run"), _dptr(success, torch.uint8, "success"),
-        _dptr(selected, torch.int16, "selected"), _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
-        _stream(stream)), "mbbp_wms_decode")
+        B.handle, batch, sp, lp, stride, iters, T, wp, gp, ep, cp, ip, okp, selp,
+        _out(workspace, torch.uint8, "workspace", 0, B.device), workspace.numel(), _stream(stream)),
+        "mbbp_wms_decode")
 
 
 def mbbp_adam_step(params, grad, m, v, lr, beta1, beta2, eps, step, lo, hi, stream=None) -> None:
     import torch
-    _check(_lib.mbbp_adam_step(_dptr(params, torch.float32, "params"), _dptr(grad, torch.float32, "grad"),
-                               _dptr(m, torch.float32, "m"), _dptr(v, torch.float32, "v"), params.numel(),
+    cnt, dev = params.numel(), params.device.index
+    _check(_lib.mbbp_adam_step(_dptr(params, torch.float32, "params"), _out(grad, torch.float32, "grad", cnt, dev),
+                               _out(m, torch.float32, "m", cnt, dev), _out(v, torch.float32, "v", cnt, dev), cnt,
                                float(lr), float(beta1), float(beta2), float(eps), int(step), float(lo), float(hi),
                                _stream(stream)), "mbbp_adam_step")
 
@@ -560,6 +628,7 @@ class Logicals:
     def __init__(self, handle: int, n: int):
         self.handle = C.c_void_p(handle)
         self.n = n
+        self.device = _current_device()
         k = C.c_int32()
         _check(_lib.mbbp_logicals_info(self.handle, C.cast(C.pointer(k), _vp), None), "mbbp_logicals_info")
         self.k = k.value
@@ -587,23 +656,27 @@ def mbbp_logicals_build(H, H_other) -> Logicals:
 def mbbp_judge(L: Logicals, e, e_hat, fail=None, counts=None, stream=None) -> None:
     import torch
     batch = e_hat.shape[0]
-    _check(_lib.mbbp_judge(L.handle, batch, _dptr(e, torch.int32, "e"), _dptr(e_hat, torch.uint8, "e_hat"),
-                           _dptr(fail, torch.uint8, "fail"), _dptr(counts, torch.int64, "counts"),
-                           _stream(stream)), "mbbp_judge")
+    n, dev = L.n, L.device
+    if e_hat.numel() != batch * n:
+        raise ValueError("e_hat must be [batch, n]")
+    _check(_lib.mbbp_judge(L.handle, batch, _out(e, torch.int32, "e", batch * ((n + 31) // 32), dev),
+                           _out(e_hat, torch.uint8, "e_hat", batch * n, dev), _out(fail, torch.uint8, "fail", batch, dev),
+                           _out(counts, torch.int64, "counts", 3, dev), _stream(stream)), "mbbp_judge")
 
 
 # ----------------------------------------------------------------- helpers
 
 def decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int = RULE_NMS,
            want_posterior: bool = False, stream=None, schedule: int = SCHEDULE_FLOODING,
-           decision: int = DECISION_FWS) -> dict:
+           decision: int = DECISION_FWS, want_c2v: bool = False) -> dict:
     """Allocate the outputs with torch and call ``mbbp_decode`` (or
     ``mbbp_decode_ex`` for the serial schedule or the LMS decision).
 
     Returns a dict of CUDA tensors: e_hat [batch, n], conv [batch, R],
     iters [batch, R] (int16 holding uint16), success [batch], selected
     [batch], cand [batch, R, W] (int32 words; a view of the workspace) and
-    posterior [batch, R, n] if requested."""
+    posterior [batch, R, n] if requested, and with want_c2v the last
+    iteration's check messages c2v [batch, R, E] (mbbp_decode_trace)."""
     import torch
     dev = syndromes.device
     batch = syndromes.shape[0]
@@ -618,7 +691,12 @@ def decode(B: Bases, syndromes, llr, iters: int, alpha: float, rule: int = RULE_
     ws = torch.empty((ws_bytes,), dtype=torch.uint8, device=dev)
     post = (torch.empty((batch, B.R, B.n), dtype=torch.float32, device=dev)
             if want_posterior else None)
-    if schedule == SCHEDULE_FLOODING and decision == DECISION_FWS:
+    if want_c2v:
+        out["c2v"] = torch.zeros((batch, B.R, int(B.edges.max())), dtype=torch.float32, device=dev)
+        opt = Options(rule, float(alpha), schedule, decision)
+        mbbp_decode_trace(B, syndromes, llr, iters, opt, out["e_hat"], out["conv"], out["success"], out["c2v"], ws,
+                          iters_run=out["iters"], selected=out["selected"], posterior=post, stream=stream)
+    elif schedule == SCHEDULE_FLOODING and decision == DECISION_FWS:
         mbbp_decode(B, syndromes, llr, iters, alpha, rule, out["e_hat"], out["conv"], out["success"], ws,
                     iters_run=out["iters"], selected=out["selected"], posterior=post, stream=stream)
     else:

@@ -43,3 +43,29 @@ def read_golden(name):
             else:
                 sections.setdefault(cur, []).append([int(t, 0) for t in toks])
     return sections
+
+
+def oracle_decode_parallel(H, sets, synd, llr, iters, alpha, rule=0, precision="f32", chunks=None, **kw):
+    """oracle.mbbp_decode over a large batch, split into shot ranges decoded
+    by host threads (the oracle's C code runs without the GIL) and
+    concatenated in shot order; identical to one call on the whole batch."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle
+    synd = np.ascontiguousarray(synd)
+    batch = synd.shape[0]
+    per_shot_llr = np.ndim(llr) == 2
+    k = chunks or min(64, max(1, (os.cpu_count() or 1) * 2))
+    edges = np.linspace(0, batch, k + 1).astype(int)
+    parts = [(a, b) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+
+    def run(ab):
+        a, b = ab
+        return oracle.mbbp_decode(H, sets, synd[a:b], llr[a:b] if per_shot_llr else llr, iters, alpha, rule,
+                                  precision=precision, **kw)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        outs = list(ex.map(run, parts))
+    return {key: np.concatenate([o[key] for o in outs]) for key in outs[0]}

@@ -243,6 +243,105 @@ def test_invalid_arguments(M):
     big = np.ones((4, 20), np.uint8)  # row weight 20 > 12
     with pytest.raises(M.MBBPError):
         M.mbbp_build_bases_from_sets(big, [[]])
+    # the binding refuses undersized or short buffers before calling the library
+    ws = torch.empty(M.mbbp_decode_workspace_size(B, 4), dtype=torch.uint8, device=dev)
+    e_hat = torch.empty((4, 72), dtype=torch.uint8, device=dev)
+    conv = torch.empty((4, 4), dtype=torch.uint8, device=dev)
+    succ = torch.empty(4, dtype=torch.uint8, device=dev)
+    bad = [dict(e_hat=e_hat[:3]), dict(conv=conv[:2]), dict(success=succ[:3]),
+           dict(llr=llr[:71]), dict(llr=torch.ones((3, 72), dtype=torch.float32, device=dev)),
+           dict(llr=torch.ones((4, 70), dtype=torch.float32, device=dev)),
+           dict(iters_run=torch.empty((4, 3), dtype=torch.int16, device=dev)),
+           dict(selected=torch.empty(3, dtype=torch.int16, device=dev)),
+           dict(posterior=torch.empty((4, 4, 71), dtype=torch.float32, device=dev))]
+    for kw in bad:
+        args = dict(e_hat=e_hat, conv=conv, success=succ, llr=llr)
+        args.update(kw)
+        extra = {k: v for k, v in args.items() if k in ("iters_run", "selected", "posterior")}
+        with pytest.raises(ValueError):
+            M.mbbp_decode(B, s, args["llr"], 5, 0.5, 0, args["e_hat"], args["conv"], args["success"], ws, **extra)
+
+
+def gpu_trace(M, B, s, llr, iters, alpha, rule):
+    """Decode through mbbp_decode_trace: outputs plus the check messages of
+    the last iteration of every (shot, representation)."""
+    import torch
+    dev = torch.device("cuda:0")
+    out = M.decode(B, torch.from_numpy(np.ascontiguousarray(s)).to(dev),
+                   torch.from_numpy(np.ascontiguousarray(llr, np.float32)).to(dev),
+                   iters, alpha, rule, want_posterior=True, want_c2v=True)
+    torch.cuda.synchronize()
+    return {"iters": out["iters"].cpu().numpy().view(np.uint16), "conv": out["conv"].cpu().numpy(),
+            "post": out["posterior"].cpu().numpy(), "c2v": out["c2v"].cpu().numpy()}
+
+
+def oracle_items(H, sets, s, llr, iters, alpha, rule, precision):
+    """Per (shot, representation): the oracle's BP on H^(t) = [H; H_t]
+    (Eq. (4)) with its syndrome [s; s_t]: (K, converged, check messages
+    numbered row by row with columns ascending, posteriors)."""
+    out = {}
+    dt = np.float64 if precision == "f64" else np.float32
+    for t, rows in enumerate(sets):
+        Ht = np.vstack([H, H[rows]]).astype(np.uint8)
+        mask = Ht.astype(bool)
+        for i in range(len(s)):
+            st = np.concatenate([s[i], s[i][rows]]).astype(np.uint8)
+            r = oracle.bp(Ht, st, np.asarray(llr, dt), iters, alpha, rule, precision=precision, want_c2v=True)
+            out[(i, t)] = (r["K"], r["conv"], r["c2v"][mask], r["post"])
+    return out
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+@pytest.mark.parametrize("code,R,shots", [("bb72", 4, 300), ("bb288", 8, 40)])
+def test_fp64_check_messages(M, rule, code, R, shots):
+    """Check-to-variable messages (Eq. (2)) and posteriors against the FP64
+    oracle, per message: |gpu - ref| <= 1e-4 max(|ref|, 1) after 1, 2 and 5
+    iterations for every (shot, representation) that stopped at the same
+    iteration, on the small-code kernel ([[72]]) and the generic kernel
+    ([[288]]).  At the last iteration of 50-iteration runs FP32 and FP64
+    trajectories of late, chaotic items separate (a property of FP32
+    arithmetic: the FP32 oracle shows the same), so there the GPU is held to
+    the FP32 oracle: bit for bit for min-sum, and for sum-product no more
+    items beyond 1e-4 of FP64 than the FP32 oracle has (plus 1% of the
+    items); both counts are printed."""
+    c = named_code(code)
+    H = c.HZ
+    n = H.shape[1]
+    ex, _ = oracle.sample(SEED, 5000, shots, n, 0.05, "depolarizing")
+    s = oracle.syndrome(H, ex)
+    B = M.mbbp_build_bases(H, R, SEED)
+    llr = channel_llr(n, 2 * 0.05 / 3)
+    for it in (1, 2, 5, 50):
+        got = gpu_trace(M, B, s, llr, it, 0.625, rule)
+        ref = oracle_items(H, B.sets, s, llr, it, 0.625, rule, "f64")
+        ref32 = oracle_items(H, B.sets, s, llr, it, 0.625, rule, "f32") if it == 50 else None
+        worst, beyond, beyond32, items, same = 0.0, 0, 0, 0, 0
+        for (i, t), (K, conv, m64, p64) in ref.items():
+            items += 1
+            if int(got["iters"][i, t]) != K or K == 0:
+                continue
+            same += 1
+            E = m64.size
+            g = got["c2v"][i, t, :E].astype(np.float64)
+            err = max(float(np.max(np.abs(g - m64) / np.maximum(np.abs(m64), 1.0))),
+                      float(np.max(np.abs(got["post"][i, t] - p64) / np.maximum(np.abs(p64), 1.0))))
+            if it < 50:
+                assert err <= 1e-4, (code, rule, it, i, t, err)
+                worst = max(worst, err)
+                continue
+            beyond += err > 1e-4
+            K32, _, m32, _ = ref32[(i, t)]
+            if K32 == K:
+                beyond32 += float(np.max(np.abs(m32 - m64) / np.maximum(np.abs(m64), 1.0))) > 1e-4
+                if rule == 0:
+                    assert np.array_equal(got["c2v"][i, t, :E], m32), (code, i, t)
+        assert same >= 0.98 * items, (it, same, items)
+        if it < 50:
+            print(f"\n{code} rule={rule} iteration {it}: {same} items, largest error {worst:.2e}")
+        else:
+            print(f"\n{code} rule={rule} 50 iterations: {same} items stopped together; beyond 1e-4 of FP64: "
+                  f"GPU {beyond}, FP32 oracle {beyond32}")
+            assert beyond <= beyond32 + max(2, 0.01 * same), (beyond, beyond32)
 
 
 @pytest.mark.parametrize("rule", [0, 1])
@@ -252,7 +351,8 @@ def test_fp64_messages_and_decisions(M, rule):
     decisions on >= 99.9% of shots for min-sum.  For sum-product the FP32
     oracle itself agrees with the FP64 oracle on fewer shots (late, chaotic
     convergence amplifies last-bit differences of expm1/log1p), so the GPU
-    must match the FP64 oracle as often as the FP32 oracle does."""
+    must match the FP64 oracle as often as the FP32 oracle does (minus
+    0.4%); the agreement rates are printed."""
     c, H, e, s = workload("bb72", "HZ", 400, 0.05, "bsc", first=5000)
     B = M.mbbp_build_bases(H, 4, SEED)
     llr = channel_llr(72, 0.05)
@@ -264,16 +364,20 @@ def test_fp64_messages_and_decisions(M, rule):
         g, r = got["posterior"][same], ref["post"][same]
         err = np.abs(g - r) / np.maximum(np.abs(r), 1.0)
         assert err.max() <= 1e-4, (it, err.max())
-    c, H, e, s = workload("bb72", "HZ", 2000, 0.05, "bsc")
-    got = gpu_decode(M, B, s, llr, 50, 0.625, rule)
-    ref = oracle.mbbp_decode(H, B.sets, s, llr, 50, 0.625, rule, precision="f64")
-    agree = (got["e_hat"] == ref["ehat"]).all(1).mean()
-    if rule == 0:
-        assert agree >= 0.999, agree
-    else:
+    for shots, first in ((2000, 0), (10000, 20000)):
+        c, H, e, s = workload("bb72", "HZ", shots, 0.05, "bsc", first=first)
+        got = gpu_decode(M, B, s, llr, 50, 0.625, rule)
+        ref = oracle.mbbp_decode(H, B.sets, s, llr, 50, 0.625, rule, precision="f64")
         f32 = oracle.mbbp_decode(H, B.sets, s, llr, 50, 0.625, rule, precision="f32")
+        agree = (got["e_hat"] == ref["ehat"]).all(1).mean()
         agree32 = (f32["ehat"] == ref["ehat"]).all(1).mean()
-        assert agree >= 0.99 and agree >= agree32 - 0.004, (agree, agree32)
+        agree_gpu32 = (got["e_hat"] == f32["ehat"]).all(1).mean()
+        print(f"\nrule={rule}, [[72]] R=4, {shots} shots: decisions agree GPU/FP64 {agree:.4%}, "
+              f"FP32 oracle/FP64 {agree32:.4%}, GPU/FP32 oracle {agree_gpu32:.4%}")
+        if rule == 0:
+            assert agree >= 0.999, agree
+        else:
+            assert agree >= 0.99 and agree >= agree32 - 0.004, (agree, agree32)
 
 
 def test_sum_product_against_fp32_oracle(M):

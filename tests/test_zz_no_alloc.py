@@ -3,8 +3,9 @@ allocate device memory (for example a decoder inside a real-time control loop,
 where an allocation could block or fail mid-run).  Its scratch is a fixed
 array inside the library, so this file checks, through the C ABI, that two
 calls in a row give exactly what mbbp_decode gives with a caller-owned
-workspace, that stale scratch from the first call does not leak into the
-second, and that a batch too large for the array is refused.  It is collected
+workspace, that stale scratch from an earlier call does not leak into a
+later one (the third call repeats the first code and size on other shots),
+and that a batch too large for the array is refused.  It is collected
 last on purpose, and passes alone in a fresh process as well."""
 import numpy as np
 import pytest
@@ -29,11 +30,15 @@ def test_noalloc_matches_workspace_decode_on_two_calls():
     import torch
     from paper_2605_14170_gb300 import mbbp
     dev = torch.device("cuda:0")
-    cases = [("bb144", "HZ", 16, 3000, 0.06, 100), ("bb72", "HX", 4, 1200, 0.05, 50)]
-    for code, which, R, batch, p, iters in cases:  # two calls in a row
+    # calls in a row: the third repeats the first code and size on other
+    # shots, so it reads a scratch region that the first call filled with
+    # different candidates (and the second overwrote only in part)
+    cases = [("bb144", "HZ", 16, 3000, 0.06, 100, 777), ("bb72", "HX", 4, 1200, 0.05, 50, 777),
+             ("bb144", "HZ", 16, 3000, 0.07, 100, 778)]
+    for code, which, R, batch, p, iters, seed in cases:
         c = named_code(code)
         H = getattr(c, which)
-        ex, ez = oracle.sample(777, 0, batch, H.shape[1], p, "depolarizing")
+        ex, ez = oracle.sample(seed, 0, batch, H.shape[1], p, "depolarizing")
         s = oracle.syndrome(H, ex if which == "HZ" else ez)
         llr = torch.from_numpy(channel_llr(H.shape[1], 2 * p / 3).astype(np.float32)).to(dev)
         syn = torch.from_numpy(s).to(dev)
