@@ -166,6 +166,52 @@ __device__ __forceinline__ float var_dispatch(int deg, float* msg, const uint16_
     }
 }
 
+// Byte offset of slot i (0..5) of a packed width-6 descriptor (vdesc6).
+__device__ __forceinline__ uint32_t packed_off(const uint4& d, int i) {
+    const uint32_t w = (i < 2) ? d.y : (i < 4 ? d.z : d.w);
+    return (i & 1) ? (w >> 16) : (w & 0xffffu);
+}
+
+__device__ __forceinline__ float& msg_at(float* msg, uint32_t byte_off) {
+    return *reinterpret_cast<float*>(reinterpret_cast<char*>(msg) + byte_off);
+}
+
+// var_update with the slots taken from a packed descriptor: the same sums in
+// the same order, without the slot-list load.
+template <int D>
+__device__ __forceinline__ float var_update_packed(float* msg, const uint4& d, float mu) {
+    uint32_t a[D];
+    float m[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) a[i] = packed_off(d, i);
+#pragma unroll
+    for (int i = 0; i < D; ++i) m[i] = msg_at(msg, a[i]);
+    float P[D + 1];
+    P[0] = mu;
+#pragma unroll
+    for (int i = 0; i < D; ++i) P[i + 1] = __fadd_rn(P[i], m[i]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float q = P[i];
+#pragma unroll
+        for (int k = i + 1; k < D; ++k) q = __fadd_rn(q, m[k]);
+        msg_at(msg, a[i]) = q;
+    }
+    return P[D];
+}
+
+__device__ __forceinline__ float var_dispatch_packed(int deg, float* msg, const uint4& d, float mu) {
+    switch (deg) {
+        case 1: return var_update_packed<1>(msg, d, mu);
+        case 2: return var_update_packed<2>(msg, d, mu);
+        case 3: return var_update_packed<3>(msg, d, mu);
+        case 4: return var_update_packed<4>(msg, d, mu);
+        case 5: return var_update_packed<5>(msg, d, mu);
+        case 6: return var_update_packed<6>(msg, d, mu);
+        default: return mu;
+    }
+}
+
 
 // Bit-pack the hard decision eh[0..n) into the candidate words of `item`,
 // and store the convergence flag and iteration count.
@@ -226,12 +272,25 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
     }
     __syncwarp();
     // q^(0)_{v->c} = mu_v
-    for (int p = lane; p < n; p += 32) {
-        const uint2 d = __ldg(vd + p);
-        const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
-        const float x = mu_s[v];
-        for (int i = 0; i < deg; ++i) msg[__ldg(B.vslot + d.x + i)] = x;
-        if (io.post) io.post[item * n + v] = x;
+    if constexpr (DC == 6) {
+        const uint4* vd6 = B.vdesc6 + (size_t)b * n;
+        for (int p = lane; p < n; p += 32) {
+            const uint4 d = __ldg(vd6 + p);
+            const int v = d.x & 0xffff, deg = (int)(d.x >> 16);
+            const float x = mu_s[v];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                if (i < deg) msg_at(msg, packed_off(d, i)) = x;
+            if (io.post) io.post[item * n + v] = x;
+        }
+    } else {
+        for (int p = lane; p < n; p += 32) {
+            const uint2 d = __ldg(vd + p);
+            const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
+            const float x = mu_s[v];
+            for (int i = 0; i < deg; ++i) msg[__ldg(B.vslot + d.x + i)] = x;
+            if (io.post) io.post[item * n + v] = x;
+        }
     }
     __syncwarp();
 
@@ -277,15 +336,29 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
         }
         __syncwarp();
         // variable pass, posterior, hard decision; each step's descriptor is
-        // loaded one step ahead, so only the slot-list load waits on L1
-        uint2 dn = (lane < n) ? __ldg(vd + lane) : make_uint2(0u, 0u);
-        for (int p = lane; p < n; p += 32) {
-            const uint2 d = dn;
-            if (p + 32 < n) dn = __ldg(vd + p + 32);
-            const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
-            const float post = var_dispatch<1, DV>(deg, msg, B.vslot + d.x, mu_s[v]);
-            eh[v] = (post < 0.f) ? 1 : 0;
-            if (io.post) io.post[item * n + v] = post;
+        // loaded one step ahead (width 6: with the slots packed in, so no load
+        // of the pass waits on L1; other widths: the slot list still does)
+        if constexpr (DC == 6) {
+            const uint4* vd6 = B.vdesc6 + (size_t)b * n;
+            uint4 dn = (lane < n) ? __ldg(vd6 + lane) : make_uint4(0u, 0u, 0u, 0u);
+            for (int p = lane; p < n; p += 32) {
+                const uint4 d = dn;
+                if (p + 32 < n) dn = __ldg(vd6 + p + 32);
+                const int v = d.x & 0xffff, deg = (int)(d.x >> 16);
+                const float post = var_dispatch_packed(deg, msg, d, mu_s[v]);
+                eh[v] = (post < 0.f) ? 1 : 0;
+                if (io.post) io.post[item * n + v] = post;
+            }
+        } else {
+            uint2 dn = (lane < n) ? __ldg(vd + lane) : make_uint2(0u, 0u);
+            for (int p = lane; p < n; p += 32) {
+                const uint2 d = dn;
+                if (p + 32 < n) dn = __ldg(vd + p + 32);
+                const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
+                const float post = var_dispatch<1, DV>(deg, msg, B.vslot + d.x, mu_s[v]);
+                eh[v] = (post < 0.f) ? 1 : 0;
+                if (io.post) io.post[item * n + v] = post;
+            }
         }
         __syncwarp();
     }

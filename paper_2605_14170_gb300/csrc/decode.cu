@@ -42,15 +42,20 @@ decode_kernel(const DecodeArgs a) {
     unsigned char* area = smem + L.hcol_bytes + warp * L.per_warp;
     for (int i = threadIdx.x; i < DC * B.mpad; i += blockDim.x) hcol_s[i] = __ldg(B.hcol + i);
     __syncthreads();
+    // Work items are taken representation-major (item = b * batch + shot):
+    // the warps resident at one time mostly decode the same representation,
+    // so its descriptor tables stay in L1 instead of one table per warp.
+    const unsigned long long batch = (unsigned long long)a.io.batch;
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.counter, 1ull);
         item = __shfl_sync(kFull, item, 0);
         if (item >= a.total_items) break;
-        const int shot = (int)(item / (unsigned long long)R);
-        const int b = (int)(item - (unsigned long long)shot * R);
+        const int b = (int)(item / batch);
+        const int shot = (int)(item - (unsigned long long)b * batch);
         generic_bp::run_item<DC, DV, RULE, TRACE>(B, a.io, shot, b, area, hcol_s);
     }
+    (void)R;
 }
 
 // The serial-schedule kernel: same work list as decode_kernel, one warp per

@@ -503,6 +503,10 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     std::vector<int32_t> rowptr((size_t)R * MP, 0);
     std::vector<uint2> vdesc((size_t)R * n);
     std::vector<uint16_t> vslot;
+    // width 6: the slot list packed into the descriptor itself (byte offsets
+    // of up to 6 slots, ascending row), so the variable pass needs no second
+    // dependent load
+    std::vector<uint4> vdesc6(K == 6 ? (size_t)R * n : 0, make_uint4(0, 0, 0, 0));
     std::vector<int32_t> rows(R), edges(R);
     std::vector<uint2> evar((size_t)R * K * MP, make_uint2(0, 0));
     // chunked serial path (widths 6 and 8): per-edge and per-variable slot
@@ -544,6 +548,11 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
             vdesc[(size_t)t * n + p] = d;
             vstart[v] = d;
             vslot.insert(vslot.end(), vl[v].begin(), vl[v].end());
+            if (K == 6) {
+                uint32_t o[6] = {0, 0, 0, 0, 0, 0};
+                for (int i = 0; i < (int)vl[v].size() && i < 6; ++i) o[i] = 4u * vl[v][i];
+                vdesc6[(size_t)t * n + p] = make_uint4(d.y, o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16));
+            }
         }
         // Serial schedule: every edge slot points at its variable's slot list;
         // rows go, in row order, into the first layer holding none of their
@@ -711,7 +720,8 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     const size_t o_lpos = o_vdesc3 + align256(vdesc3.size() * sizeof(uint4));
     const size_t o_rinfo_s = o_lpos + align256(lpos.size() * 2);
     const size_t o_sedge = o_rinfo_s + align256(rinfo_s.size() * 4);
-    const size_t total = o_sedge + align256(sedge.size() * 4);
+    const size_t o_vdesc6 = o_sedge + align256(sedge.size() * 4);
+    const size_t total = o_vdesc6 + align256(vdesc6.size() * sizeof(uint4));
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
     if (e == cudaSuccess) e = cudaMalloc(&B->dmem, total);
@@ -740,6 +750,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         {o_lpos, lpos.data(), lpos.size() * 2},
         {o_rinfo_s, rinfo_s.data(), rinfo_s.size() * 4},
         {o_sedge, sedge.data(), sedge.size() * 4},
+        {o_vdesc6, vdesc6.data(), vdesc6.size() * sizeof(uint4)},
     };
     for (const Copy& c : copies) {
         if (c.bytes == 0) continue;
@@ -768,6 +779,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
     d.rinfo2 = shape ? reinterpret_cast<const uint32_t*>(base + o_rinfo2) : nullptr;
     d.hmask2 = shape ? reinterpret_cast<const uint32_t*>(base + o_hmask2) : nullptr;
     d.sedge = shape ? reinterpret_cast<const int32_t*>(base + o_sedge) : nullptr;
+    d.vdesc6 = K == 6 ? reinterpret_cast<const uint4*>(base + o_vdesc6) : nullptr;
     d.lrows = reinterpret_cast<const uint16_t*>(base + o_lrows);
     d.lptr = reinterpret_cast<const uint16_t*>(base + o_lptr);
     d.nlayers = reinterpret_cast<const int32_t*>(base + o_nlayers);

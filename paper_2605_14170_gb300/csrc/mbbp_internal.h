@@ -26,6 +26,8 @@ struct DevBases {
     const uint2* vdesc;       // [R][n]  x = first slot-list entry, y = variable | degree << 16;
                               //         variables sorted by degree (stable)
     const uint16_t* vslot;    // slot ids of every variable, ascending row of H^(t)
+    const uint4* vdesc6;      // width 6 only: [R][n] in vdesc order, x = vdesc.y, y/z/w = byte
+                              //         offsets (4 * slot id) of the variable's slots, 2 per word
     const int32_t* rows;      // [R] rows of H^(t)
     const int32_t* rowptr;    // [R][MP] first edge of each row (edges numbered row by row)
     const uint16_t* hcol;     // [DC][mpad] columns of the rows of H (n = padding)
@@ -117,6 +119,8 @@ constexpr int kNumSmallShapes = 3;
 __host__ __device__ constexpr int small_min_blocks(int RS, int rule) {
     return (RS <= 3 && rule == MBBP_RULE_NMS) ? 18 : 16;
 }
+// The same for the two-shots-per-warp kernels (normalized min-sum).
+__host__ __device__ constexpr int small_min_blocks_pair(int RS) { return RS <= 3 ? 16 : 14; }
 
 // Inputs and per-representation outputs of one code's batch of shots.
 struct ShotIO {
