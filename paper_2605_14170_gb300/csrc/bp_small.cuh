@@ -54,7 +54,7 @@ __device__ __forceinline__ void sts(char* smc, uint32_t off, float v) {
 template <int K, int RULE, bool REG, bool TRACE>
 __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const uint32_t (&cb)[K],
                                           int k, int deg, bool valid, uint32_t sbit, float alpha,
-                                          float* tr, const int32_t* se, int MP, uint32_t soff = 0) {
+                                          float* tr, const int32_t* se, int MP) {
     const int lane = threadIdx.x & 31;
     uint32_t sx = sbit << 31;
 #pragma unroll
@@ -76,7 +76,7 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
             const uint32_t mag = __float_as_uint(__fmul_rn(alpha, excl));
             const uint32_t out = mag ^ ((sx ^ __float_as_uint(q[j])) & 0x80000000u);
             if (valid && (REG || j < deg)) {
-                sts(smc, cb[j] + 128 * k + soff, __uint_as_float(out));
+                sts(smc, cb[j] + 128 * k, __uint_as_float(out));
                 if (TRACE) tr[__ldg(se + j * MP + ((lane + slot_rot(j)) & 31) + 32 * k)] = __uint_as_float(out);
             }
         }
@@ -94,7 +94,7 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
             const float mag = fminf(phi(sum), MBBP_SP_MAX);
             const uint32_t out = (__float_as_uint(mag) ^ sx) ^ (__float_as_uint(q[j]) & 0x80000000u);
             if (valid && (REG || j < deg)) {
-                sts(smc, cb[j] + 128 * k + soff, __uint_as_float(out));
+                sts(smc, cb[j] + 128 * k, __uint_as_float(out));
                 if (TRACE) tr[__ldg(se + j * MP + ((lane + slot_rot(j)) & 31) + 32 * k)] = __uint_as_float(out);
             }
             pre = __fadd_rn(pre, f[j]);
@@ -102,42 +102,54 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
     }
 }
 
-// Variable update of a degree-D variable (Eq. (3), ascending row order of
-// H^(t)); returns the posterior.  The clamp of q to [-LMAX, LMAX] is not
-// applied here because nothing observable depends on it: q only feeds the
-// check rule, whose min also runs over LMAX (so |q| >= LMAX and LMAX give the
-// same message and sign), and phi(|q|) underflows to 0 for |q| >= 104 under
-// either value; q stays finite (|q| <= |mu| + 6 LMAX).
-template <int D>
-__device__ __forceinline__ float var_upd(char* smc, const uint4& d, float mu) {
-    uint32_t a[D];
-    float m[D];
+// Variable update (Eq. (3)): q_i = mu + the other messages of the variable in
+// ascending row order of H^(t), posterior = mu + all of them.  The clamp of q
+// to [-LMAX, LMAX] is not applied here because nothing observable depends on
+// it: q only feeds the check rule, whose min also runs over LMAX (so
+// |q| >= LMAX and LMAX give the same message and sign), and phi(|q|)
+// underflows to 0 for |q| >= 104 under either value; q stays finite
+// (|q| <= |mu| + 6 LMAX).
+//
+// The update runs for the 32 lanes of a variable step at once: DM is the largest
+// degree among the step's lanes (warp-uniform), and a lane of degree
+// deg <= DM runs the same instructions with its edges i >= deg predicated
+// off, which loads, adds and stores nothing for it.  Each lane's sums are
+// therefore those of its own degree (same terms, same order), while the step
+// issues one load and one store instruction per edge position instead of one
+// per degree case present among its lanes.
+template <int DM>
+__device__ __forceinline__ float var_upd_step(char* smc, const uint4& d, float mu, int deg) {
+    uint32_t a[DM];
+    float m[DM];
 #pragma unroll
-    for (int i = 0; i < D; ++i) a[i] = addr_of(d, i);
+    for (int i = 0; i < DM; ++i) a[i] = addr_of(d, i);
 #pragma unroll
-    for (int i = 0; i < D; ++i) m[i] = lds(smc, a[i]);
-    float P[D + 1];
+    for (int i = 0; i < DM; ++i) m[i] = (i < deg) ? lds(smc, a[i]) : 0.0f;
+    float P[DM + 1];  // P[i] = mu + m_0 + ... + m_{min(i, deg)-1}
     P[0] = mu;
 #pragma unroll
-    for (int i = 0; i < D; ++i) P[i + 1] = __fadd_rn(P[i], m[i]);
+    for (int i = 0; i < DM; ++i) P[i + 1] = (i < deg) ? __fadd_rn(P[i], m[i]) : P[i];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        float q = P[i];
+    for (int i = 0; i < DM; ++i) {
+        if (i < deg) {
+            float q = P[i];
 #pragma unroll
-        for (int t = i + 1; t < D; ++t) q = __fadd_rn(q, m[t]);
-        sts(smc, a[i], q);
+            for (int t = i + 1; t < DM; ++t)
+                if (t < deg) q = __fadd_rn(q, m[t]);
+            sts(smc, a[i], q);
+        }
     }
-    return P[D];
+    return P[DM];
 }
 
-__device__ __forceinline__ float var_step(char* smc, int deg, const uint4& d, float mu) {
-    switch (deg) {
-        case 1: return var_upd<1>(smc, d, mu);
-        case 2: return var_upd<2>(smc, d, mu);
-        case 3: return var_upd<3>(smc, d, mu);
-        case 4: return var_upd<4>(smc, d, mu);
-        case 5: return var_upd<5>(smc, d, mu);
-        case 6: return var_upd<6>(smc, d, mu);
+__device__ __forceinline__ float var_step(char* smc, int dmax, int deg, const uint4& d, float mu) {
+    switch (dmax) {
+        case 1: return var_upd_step<1>(smc, d, mu, deg);
+        case 2: return var_upd_step<2>(smc, d, mu, deg);
+        case 3: return var_upd_step<3>(smc, d, mu, deg);
+        case 4: return var_upd_step<4>(smc, d, mu, deg);
+        case 5: return var_upd_step<5>(smc, d, mu, deg);
+        case 6: return var_upd_step<6>(smc, d, mu, deg);
         default: return mu;
     }
 }
@@ -169,7 +181,9 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
     // degrees, 4 bits per variable step; variable ids are re-read from L1
     // when a shot starts and ends
     uint4 desc[VS];
-    static_assert(VS <= 8 && RS <= 8, "degrees are packed 4 bits per step in 32 bits");
+    static_assert(VS <= 5 && RS <= 8, "degrees are packed 3 bits per step, twice, in 32 bits");
+    // this lane's degree (bits 3k..3k+2) and the step's largest degree
+    // (bits 16+3k..) of every variable step k; degrees are at most 6
     uint32_t degs = 0;
 #pragma unroll
     for (int k = 0; k < VS; ++k) {
@@ -177,7 +191,8 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
         desc[k].y += wshift;
         desc[k].z += wshift;
         desc[k].w += wshift;
-        degs |= (desc[k].x >> 16) << (4 * k);
+        const uint32_t dk = desc[k].x >> 16;
+        degs |= (dk << (3 * k)) | (__reduce_max_sync(kFull, dk) << (16 + 3 * k));
     }
 #pragma unroll
     for (int k = 0; k < ORS; ++k)
@@ -219,7 +234,7 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
         // q^(0) = mu on every edge
 #pragma unroll
         for (int k = 0; k < VS; ++k) {
-            const int deg = (int)((degs >> (4 * k)) & 0xfu);
+            const int deg = (int)((degs >> (3 * k)) & 7u);
 #pragma unroll
             for (int i = 0; i < K; ++i)
                 if (i < deg) sts(smc, addr_of(desc[k], i), mu[k]);
@@ -288,8 +303,8 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
 #pragma unroll
             for (int k = 0; k < VS; ++k) {
                 if (32 * k < n) {
-                    const int deg = (int)((degs >> (4 * k)) & 0xfu);
-                    const float post = var_step(smc, deg, desc[k], mu[k]);
+                    const int deg = (int)((degs >> (3 * k)) & 7u);
+                    const float post = var_step(smc, (int)((degs >> (16 + 3 * k)) & 7u), deg, desc[k], mu[k]);
                     ew[k] = __ballot_sync(kFull, post < 0.f);
                     if (io.post && 32 * k + lane < n)
                         io.post[item * n + (__ldg(&vd[32 * k + lane].x) & 0xffffu)] = post;
@@ -320,368 +335,6 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
             if (io.iters_run) io.iters_run[item] = (uint16_t)K_run;
         }
         __syncwarp();
-    }
-}
-
-
-// ---------------------------------------------------------------------------
-// Two shots per warp.  A warp keeps two shots of its chunk in flight, each
-// in its own message area (the second at byte offset soff from the first,
-// same layout, so both see the same bank pattern), and runs one iteration
-// of both in one pass: every descriptor, address and degree case is shared,
-// and the two shots' dependency chains interleave.  A slot whose shot halts
-// (H e = s, or the iteration limit) stores its outputs and takes the next
-// shot of the chunk at once, so the two slots drift apart in iteration
-// count; once the chunk is empty the other slot finishes alone.  Every shot
-// goes through exactly the arithmetic of run_chunk, so the outputs are the
-// same bit for bit.
-
-template <int VS>
-struct PairSlot {
-    uint32_t ew[VS];   // hard decisions, one ballot word per variable step
-    uint32_t sb, sbo;  // syndrome bits: rows of H^(t) by ELL index, rows of H
-    int shot, it;      // shot (-1: empty) and iterations run
-};
-
-// The halting test H e = s of a slot (first row group first, as run_chunk).
-template <int VS, int ORS>
-__device__ __forceinline__ bool pair_halted(const PairSlot<VS>& S, const uint32_t* hms) {
-    const int lane = threadIdx.x & 31;
-    bool ok;
-    {
-        uint32_t acc = 0;
-#pragma unroll
-        for (int w = 0; w < VS; ++w) acc ^= hms[w * (ORS * 32) + lane] & S.ew[w];
-        ok = ((__popc(acc) ^ S.sbo) & 1u) == 0u;
-    }
-    bool conv_now = __all_sync(kFull, ok);
-    if (ORS > 1 && conv_now) {
-#pragma unroll
-        for (int k = 1; k < ORS; ++k) {
-            uint32_t acc = 0;
-#pragma unroll
-            for (int w = 0; w < VS; ++w) acc ^= hms[w * (ORS * 32) + lane + 32 * k] & S.ew[w];
-            ok = ok && (((__popc(acc) ^ (S.sbo >> k)) & 1u) == 0u);
-        }
-        conv_now = __all_sync(kFull, ok);
-    }
-    return conv_now;
-}
-
-// Start shot `shot` in the slot at byte offset soff: LLRs, syndrome bits,
-// q^(0) = mu on every edge.
-template <int VS, int RS, int ORS>
-__device__ __forceinline__ void pair_load(const DevBases& B, const ShotIO& io, int b, int shot, PairSlot<VS>& S,
-                                          char* smc, uint32_t soff, float* mus, const uint4 (&desc)[VS],
-                                          uint32_t degs, const uint4* vd, const uint32_t* ri, int Mb) {
-    const int lane = threadIdx.x & 31;
-    const int n = B.n, m = B.m;
-    const float* llr = io.llr + (size_t)shot * io.llr_stride;
-    const uint8_t* sy = io.synd + (size_t)shot * m;
-    S.shot = shot;
-    S.it = 0;
-    float mu[VS];
-#pragma unroll
-    for (int k = 0; k < VS; ++k) {
-        const bool live = (32 * k + lane) < n;
-        const uint32_t v = __ldg(&vd[32 * k + lane].x) & 0xffffu;
-        mu[k] = live ? __fadd_rn(__ldg(llr + v), 0.0f) : 0.0f;
-        mus[32 * k + lane] = mu[k];
-        S.ew[k] = __ballot_sync(kFull, mu[k] < 0.f);
-    }
-    S.sb = 0;
-    S.sbo = 0;
-#pragma unroll
-    for (int k = 0; k < RS; ++k)
-        if (lane + 32 * k < Mb) S.sb |= (uint32_t)(__ldg(sy + (__ldg(ri + lane + 32 * k) & 0xffffu)) & 1u) << k;
-#pragma unroll
-    for (int k = 0; k < ORS; ++k)
-        if (lane + 32 * k < m) S.sbo |= (uint32_t)(__ldg(sy + lane + 32 * k) & 1u) << k;
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < VS; ++k) {
-        const int deg = (int)((degs >> (4 * k)) & 0xfu);
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-            if (i < deg) sts(smc, addr_of(desc[k], i) + soff, mu[k]);
-    }
-    __syncwarp();
-}
-
-// Outputs of a halted slot (candidate bits through its own message area,
-// which no other shot uses until the slot is refilled).
-template <int VS>
-__device__ __forceinline__ void pair_store(const DevBases& B, const ShotIO& io, int b, const PairSlot<VS>& S,
-                                           bool conv, char* area, const uint4* vd) {
-    const int lane = threadIdx.x & 31;
-    const int n = B.n;
-    const unsigned long long item = (unsigned long long)S.shot * B.R + b;
-    __syncwarp();
-    uint8_t* ebytes = reinterpret_cast<uint8_t*>(area);
-#pragma unroll
-    for (int k = 0; k < VS; ++k)
-        if (32 * k + lane < n) ebytes[__ldg(&vd[32 * k + lane].x) & 0xffffu] = (uint8_t)((S.ew[k] >> lane) & 1u);
-    __syncwarp();
-    uint32_t myword = 0;
-#pragma unroll
-    for (int w = 0; w < VS; ++w) {
-        const int v = 32 * w + lane;
-        const uint32_t word = __ballot_sync(kFull, v < n && ebytes[v]);
-        if (lane == w) myword = word;
-    }
-    const int W = (n + 31) >> 5;
-    if (lane < W) io.cand[item * W + lane] = myword;
-    if (lane == 0) {
-        io.conv[item] = conv ? 1 : 0;
-        if (io.iters_run) io.iters_run[item] = (uint16_t)S.it;
-    }
-    __syncwarp();
-}
-
-// Variable update of a degree-D variable for both slots.
-template <int D>
-__device__ __forceinline__ void var_upd_pair(char* smc, const uint4& d, uint32_t soff, float mua, float mub,
-                                             float& pa, float& pb) {
-    uint32_t a[D];
-    float ma[D], mb[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) a[i] = addr_of(d, i);
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        ma[i] = lds(smc, a[i]);
-        mb[i] = lds(smc, a[i] + soff);
-    }
-    float Pa[D + 1], Pb[D + 1];
-    Pa[0] = mua;
-    Pb[0] = mub;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        Pa[i + 1] = __fadd_rn(Pa[i], ma[i]);
-        Pb[i + 1] = __fadd_rn(Pb[i], mb[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        float qa = Pa[i], qb = Pb[i];
-#pragma unroll
-        for (int t = i + 1; t < D; ++t) {
-            qa = __fadd_rn(qa, ma[t]);
-            qb = __fadd_rn(qb, mb[t]);
-        }
-        sts(smc, a[i], qa);
-        sts(smc, a[i] + soff, qb);
-    }
-    pa = Pa[D];
-    pb = Pb[D];
-}
-
-__device__ __forceinline__ void var_step_pair(char* smc, int deg, const uint4& d, uint32_t soff, float mua,
-                                              float mub, float& pa, float& pb) {
-    switch (deg) {
-        case 1: var_upd_pair<1>(smc, d, soff, mua, mub, pa, pb); return;
-        case 2: var_upd_pair<2>(smc, d, soff, mua, mub, pa, pb); return;
-        case 3: var_upd_pair<3>(smc, d, soff, mua, mub, pa, pb); return;
-        case 4: var_upd_pair<4>(smc, d, soff, mua, mub, pa, pb); return;
-        case 5: var_upd_pair<5>(smc, d, soff, mua, mub, pa, pb); return;
-        case 6: var_upd_pair<6>(smc, d, soff, mua, mub, pa, pb); return;
-        default: pa = mua; pb = mub; return;
-    }
-}
-
-// One iteration of one slot (the other is empty).
-template <int VS, int RS, int RULE, bool REG>
-__device__ __forceinline__ void pair_iter1(const DevBases& B, const ShotIO& io, int b, PairSlot<VS>& S,
-                                           char* smc, uint32_t soff, const float* mus, const uint32_t (&cb)[6],
-                                           const uint4 (&desc)[VS], uint32_t degs, uint32_t rowdeg,
-                                           const uint4* vd, int Mb) {
-    constexpr int K = 6;
-    const int lane = threadIdx.x & 31;
-    const int n = B.n;
-    float q[RS][K];
-#pragma unroll
-    for (int k = 0; k < RS; ++k) {
-        if (32 * k < Mb) {
-            const int deg = REG ? K : (int)((rowdeg >> (4 * k)) & 0xfu);
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-                q[k][j] = (REG || j < deg) ? lds(smc, cb[j] + 128 * k + soff) : MBBP_LMAX;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < RS; ++k) {
-        if (32 * k < Mb) {
-            const bool valid = lane + 32 * k < Mb;
-            const int deg = REG ? K : (int)((rowdeg >> (4 * k)) & 0xfu);
-            check_row<K, RULE, REG, false>(smc, q[k], cb, k, deg, valid, (S.sb >> k) & 1u, io.alpha, nullptr,
-                                           nullptr, B.MP, soff);
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < VS; ++k) {
-        if (32 * k < n) {
-            const int deg = (int)((degs >> (4 * k)) & 0xfu);
-            uint4 d = desc[k];
-            d.y += soff | (soff << 16);
-            d.z += soff | (soff << 16);
-            d.w += soff | (soff << 16);
-            const float post = var_step(smc, deg, d, mus[32 * k + lane]);
-            S.ew[k] = __ballot_sync(kFull, post < 0.f);
-        }
-    }
-    __syncwarp();
-}
-
-// One iteration of both slots.
-template <int VS, int RS, int RULE, bool REG>
-__device__ __forceinline__ void pair_iter2(const DevBases& B, const ShotIO& io, int b, PairSlot<VS>& S0,
-                                           PairSlot<VS>& S1, char* smc, uint32_t soff, const float* mus0,
-                                           const float* mus1, const uint32_t (&cb)[6],
-                                           const uint4 (&desc)[VS], uint32_t degs, uint32_t rowdeg,
-                                           const uint4* vd, int Mb) {
-    constexpr int K = 6;
-    const int lane = threadIdx.x & 31;
-    const int n = B.n;
-    // check pass: row step by row step, the first slot's rows then the
-    // second's (the loads of one overlap the other's arithmetic)
-#pragma unroll
-    for (int k = 0; k < RS; ++k) {
-        if (32 * k < Mb) {
-            const int deg = REG ? K : (int)((rowdeg >> (4 * k)) & 0xfu);
-            const bool valid = lane + 32 * k < Mb;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t so = h ? soff : 0u;
-                float q[K];
-#pragma unroll
-                for (int j = 0; j < K; ++j) q[j] = (REG || j < deg) ? lds(smc, cb[j] + 128 * k + so) : MBBP_LMAX;
-                check_row<K, RULE, REG, false>(smc, q, cb, k, deg, valid, ((h ? S1.sb : S0.sb) >> k) & 1u, io.alpha,
-                                               nullptr, nullptr, B.MP, so);
-            }
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < VS; ++k) {
-        if (32 * k < n) {
-            const int deg = (int)((degs >> (4 * k)) & 0xfu);
-            float pa, pb;
-            // opaque copy: keeps the compiler from holding every step's
-            // extracted addresses across iterations (registers)
-            uint4 d = desc[k];
-            asm volatile("" : "+r"(d.y), "+r"(d.z), "+r"(d.w));
-            var_step_pair(smc, deg, d, soff, mus0[32 * k + lane], mus1[32 * k + lane], pa, pb);
-            S0.ew[k] = __ballot_sync(kFull, pa < 0.f);
-            S1.ew[k] = __ballot_sync(kFull, pb < 0.f);
-        }
-    }
-    __syncwarp();
-}
-
-// Keep a slot busy: take the next shot of the chunk when it is empty, and
-// store and refill while its shot has halted; on return the slot holds a
-// shot that needs another iteration, or is empty with the chunk used up.
-template <int VS, int RS, int ORS>
-__device__ __forceinline__ void pair_service(const DevBases& B, const ShotIO& io, int b, PairSlot<VS>& S,
-                                             int& next, int shot_end, char* smc, uint32_t wbase, uint32_t so,
-                                             float* mus, const uint4 (&desc)[VS], uint32_t degs,
-                                             const uint4* vd, const uint32_t* ri, int Mb, const uint32_t* hms) {
-    for (;;) {
-        if (S.shot < 0) {
-            if (next >= shot_end) return;
-            pair_load<VS, RS, ORS>(B, io, b, next++, S, smc, so, mus, desc, degs, vd, ri, Mb);
-        }
-        const bool conv = pair_halted<VS, ORS>(S, hms);
-        if (!conv && S.it < io.iters) return;
-        pair_store<VS>(B, io, b, S, conv, smc + wbase + so, vd);
-        S.shot = -1;
-    }
-}
-
-// Shared memory of one warp of the two-slot path (floats): two message
-// areas (each K*MP messages and a zero slot padded to 16 B), the
-// halting-test masks, then the two slots' LLRs by variable position.
-__host__ __device__ constexpr int warp_floats_pair(int MP, int VS, int ORS) {
-    return 2 * (6 * MP + 4) + VS * ORS * 32 + 2 * VS * 32;
-}
-
-// run_chunk with two shots in flight (same outputs bit for bit); no
-// posterior or message output (those calls take run_chunk).
-template <int VS, int RS, int ORS, int RULE, bool REG>
-__device__ __forceinline__ void run_chunk_pair(const DevBases& B, const ShotIO& io, int b, int shot_begin,
-                                               int shot_end, char* smc, uint32_t wbase) {
-    constexpr int K = 6;
-    const int lane = threadIdx.x & 31;
-    const int MP = B.MP;
-    const uint32_t soff = 4u * (uint32_t)(K * MP + 4);
-    float* msg = reinterpret_cast<float*>(smc + wbase);
-    uint32_t* hms = reinterpret_cast<uint32_t*>(msg + 2 * (K * MP + 4));  // [VS][ORS*32]
-    float* mus0 = msg + 2 * (K * MP + 4) + VS * ORS * 32;                    // [VS*32] per slot
-    float* mus1 = mus0 + VS * 32;
-    uint32_t cb[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) cb[j] = wbase + 4u * (uint32_t)(j * MP + ((lane + slot_rot(j)) & 31));
-    const uint32_t wshift = wbase | (wbase << 16);
-    const int Mb = __ldg(B.rows + b);
-    const uint4* vd = B.vdesc2 + (size_t)b * (VS * 32);
-    const uint32_t* ri = B.rinfo2 + (size_t)b * MP;
-    const uint32_t* hm = B.hmask2 + (size_t)b * VS * (ORS * 32);
-
-    __syncwarp();
-    if (lane == 0) {
-        msg[K * MP] = 0.0f;
-        msg[2 * K * MP + 4] = 0.0f;
-    }
-    uint4 desc[VS];
-    static_assert(VS <= 8 && RS <= 8, "degrees are packed 4 bits per step in 32 bits");
-    uint32_t degs = 0;
-#pragma unroll
-    for (int k = 0; k < VS; ++k) {
-        desc[k] = __ldg(vd + 32 * k + lane);
-        desc[k].y += wshift;
-        desc[k].z += wshift;
-        desc[k].w += wshift;
-        degs |= (desc[k].x >> 16) << (4 * k);
-    }
-#pragma unroll
-    for (int k = 0; k < ORS; ++k)
-#pragma unroll
-        for (int w = 0; w < VS; ++w)
-            hms[w * (ORS * 32) + lane + 32 * k] = __ldg(hm + w * (ORS * 32) + lane + 32 * k);
-    uint32_t rowdeg = 0;
-    if (!REG) {
-#pragma unroll
-        for (int k = 0; k < RS; ++k) {
-            const int idx = lane + 32 * k;
-            if (idx < Mb) rowdeg |= ((__ldg(ri + idx) >> 16) & 0xfu) << (4 * k);
-        }
-    }
-    __syncwarp();
-
-    PairSlot<VS> S0, S1;
-    S0.shot = -1;
-    S1.shot = -1;
-    S0.it = S1.it = 0;
-    int next = shot_begin;
-    for (;;) {
-        // each slot: take the next shot when empty; store and refill while
-        // its shot has halted
-        pair_service<VS, RS, ORS>(B, io, b, S0, next, shot_end, smc, wbase, 0u, mus0, desc, degs, vd, ri, Mb, hms);
-        pair_service<VS, RS, ORS>(B, io, b, S1, next, shot_end, smc, wbase, soff, mus1, desc, degs, vd, ri, Mb,
-                                  hms);
-        const bool l0 = S0.shot >= 0, l1 = S1.shot >= 0;
-        if (l0 && l1) {
-            pair_iter2<VS, RS, RULE, REG>(B, io, b, S0, S1, smc, soff, mus0, mus1, cb, desc, degs, rowdeg, vd, Mb);
-            ++S0.it;
-            ++S1.it;
-        } else if (l0) {
-            pair_iter1<VS, RS, RULE, REG>(B, io, b, S0, smc, 0u, mus0, cb, desc, degs, rowdeg, vd, Mb);
-            ++S0.it;
-        } else if (l1) {
-            pair_iter1<VS, RS, RULE, REG>(B, io, b, S1, smc, soff, mus1, cb, desc, degs, rowdeg, vd, Mb);
-            ++S1.it;
-        } else {
-            break;
-        }
     }
 }
 

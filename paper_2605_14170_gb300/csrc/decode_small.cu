@@ -10,8 +10,8 @@ namespace {
 constexpr int kSmallWarps = 1;  // warps per block: each warp works alone
 constexpr int kChunk = 8;       // shots per work item of a warp (same representation)
 
-template <int VS, int RS, int ORS, int RULE, bool REG, bool TRACE, bool PAIR>
-__global__ void __launch_bounds__(kSmallWarps * 32, PAIR ? small_min_blocks_pair(RS) : small_min_blocks(RS, RULE))
+template <int VS, int RS, int ORS, int RULE, bool REG, bool TRACE>
+__global__ void __launch_bounds__(kSmallWarps * 32, small_min_blocks(RS, RULE))
 decode_small_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) float smsg[];
     const DevBases& B = a.B;
@@ -19,8 +19,7 @@ decode_small_kernel(const DecodeArgs a) {
     const int warp = threadIdx.x >> 5;
     const int R = B.R;
     char* smc = reinterpret_cast<char*>(smsg);
-    const uint32_t wbase = (uint32_t)(warp * (PAIR ? small_bp::warp_floats_pair(B.MP, VS, ORS)
-                                                   : small_bp::warp_floats(B.MP, VS, ORS)) * 4);
+    const uint32_t wbase = (uint32_t)(warp * small_bp::warp_floats(B.MP, VS, ORS) * 4);
     const unsigned long long chunks_per_rep = ((unsigned long long)a.io.batch + kChunk - 1) / kChunk;
     const unsigned long long total_chunks = chunks_per_rep * (unsigned long long)R;
     for (;;) {
@@ -32,26 +31,16 @@ decode_small_kernel(const DecodeArgs a) {
         const int b = (int)(chunk - (unsigned long long)sblock * R);
         const int s0 = sblock * kChunk;
         const int s1 = min(a.io.batch, s0 + kChunk);
-        if constexpr (PAIR)
-            small_bp::run_chunk_pair<VS, RS, ORS, RULE, REG>(B, a.io, b, s0, s1, smc, wbase);
-        else
-            small_bp::run_chunk<VS, RS, ORS, RULE, REG, TRACE>(B, a.io, b, s0, s1, smc, wbase);
+        small_bp::run_chunk<VS, RS, ORS, RULE, REG, TRACE>(B, a.io, b, s0, s1, smc, wbase);
     }
 }
 
 template <int VS, int RS, int ORS, int RULE, bool REG>
 cudaError_t launch_small_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
-    // two shots per warp for normalized min-sum (the register budget of the
-    // sum-product rule leaves no room for a second slot); calls that ask for
-    // posteriors or the message trace run one shot at a time
-    const bool pair = RULE == MBBP_RULE_NMS && !a.io.c2v && !a.io.post;
-    auto kern = a.io.c2v ? decode_small_kernel<VS, RS, ORS, RULE, REG, true, false>
-                         : (pair ? decode_small_kernel<VS, RS, ORS, RULE, REG, false, true>
-                                 : decode_small_kernel<VS, RS, ORS, RULE, REG, false, false>);
+    auto kern = a.io.c2v ? decode_small_kernel<VS, RS, ORS, RULE, REG, true>
+                         : decode_small_kernel<VS, RS, ORS, RULE, REG, false>;
     const int warps = kSmallWarps;
-    const size_t smem = (size_t)warps *
-                        (pair ? small_bp::warp_floats_pair(a.B.MP, VS, ORS) : small_bp::warp_floats(a.B.MP, VS, ORS)) *
-                        sizeof(float);
+    const size_t smem = (size_t)warps * small_bp::warp_floats(a.B.MP, VS, ORS) * sizeof(float);
     int per_sm = 0;
     cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kern), warps * 32, smem, &per_sm);
     if (e != cudaSuccess) return e;

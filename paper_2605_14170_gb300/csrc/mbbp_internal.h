@@ -119,8 +119,6 @@ constexpr int kNumSmallShapes = 3;
 __host__ __device__ constexpr int small_min_blocks(int RS, int rule) {
     return (RS <= 3 && rule == MBBP_RULE_NMS) ? 18 : 16;
 }
-// The same for the two-shots-per-warp kernels (normalized min-sum).
-__host__ __device__ constexpr int small_min_blocks_pair(int RS) { return RS <= 3 ? 16 : 14; }
 
 // Inputs and per-representation outputs of one code's batch of shots.
 struct ShotIO {

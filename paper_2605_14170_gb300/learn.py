@@ -40,7 +40,7 @@ def train_wms(B: "mbbp.Bases", p: float, T: int = 25, ckpt: int = 5, batch: int 
               lr: float = 1e-3, seed: int = 20260516, alpha: float = 0.625, which: str = "X",
               w_bounds=(0.0, 2.0), g_bounds=(0.0, 0.9), all_iters: bool = True, log_every: int = 10,
               L: "mbbp.Logicals | None" = None, val_shots: int = 20000, val_every: int = 25,
-              val_iters: int = 100, val_p: float | None = None, device="cuda"):
+              val_iters: int = 100, val_p: float | None = None, keep_initial: bool = True, device="cuda"):
     """Train per-edge, per-iteration weights w and damping g of WMS on the
     representations B (built from H_Z for X errors, H_X for Z errors).
     The loss is the BCE of every iteration's posterior (all_iters, which
@@ -48,9 +48,10 @@ def train_wms(B: "mbbp.Bases", p: float, T: int = 25, ckpt: int = 5, batch: int 
     With logical operators L, the weights are scored every `val_every` steps
     by their logical failures on `val_shots` held-out shots (decoded with the
     halting rule, up to `val_iters` iterations) and the best weights seen are
-    returned, the initial (plain min-sum) weights included.  The held-out
-    shots are drawn at `val_p` (default: p), e.g. a higher error rate where
-    a strong code still fails often enough to tell weights apart.
+    returned, the initial (plain min-sum) weights included unless
+    keep_initial is False (then the best trained weights are returned).  The
+    held-out shots are drawn at `val_p` (default: p), e.g. a higher error
+    rate where a strong code still fails often enough to tell weights apart.
     Returns (w, g, history) with history = [(step, mean BCE, validation
     failures or None)]."""
     import torch
@@ -79,7 +80,7 @@ def train_wms(B: "mbbp.Bases", p: float, T: int = 25, ckpt: int = 5, batch: int 
         vsyn = torch.empty((val_shots, B.m), dtype=torch.uint8, device=device)
         mbbp.mbbp_syndrome(B, ve, vsyn)
         f0 = _failures(B, L, w, g, vsyn, ve, vllr, val_iters, device)
-        best = (f0, 0, w.clone(), g.clone())
+        best = (f0 if keep_initial else 1 << 62, 0, w.clone(), g.clone())
         history.append((0, None, f0))
     for k in range(steps):
         mbbp.mbbp_sample_errors(n, batch, k * batch, seed, p, mbbp.NOISE_DEPOLARIZING, ex, ez)
@@ -103,6 +104,16 @@ def train_wms(B: "mbbp.Bases", p: float, T: int = 25, ckpt: int = 5, batch: int 
     return w, g, history
 
 
+def two_proportion_z(k1: int, k2: int, n: int) -> float:
+    """One-sided two-proportion z statistic for k1 / n > k2 / n (pooled
+    variance; conservative for the paired shots of compare_ler, whose two
+    failure counts are positively correlated)."""
+    pp = (k1 + k2) / (2.0 * n)
+    if pp <= 0.0 or pp >= 1.0:
+        return 0.0
+    return (k1 - k2) / n / math.sqrt(2.0 * pp * (1.0 - pp) / n)
+
+
 def wilson(k: int, n: int, z: float = 1.96):
     """Wilson score interval of a binomial proportion k / n."""
     if n == 0:
@@ -111,7 +122,10 @@ def wilson(k: int, n: int, z: float = 1.96):
     d = 1 + z * z / n
     c = (ph + z * z / (2 * n)) / d
     h = z * math.sqrt(ph * (1 - ph) / n + z * z / (4 * n * n)) / d
-    return (max(0.0, c - h), min(1.0, c + h))
+    # the ends are exactly 0 and 1 at k = 0 and k = n (c - h, c + h round there)
+    lo = 0.0 if k == 0 else max(0.0, c - h)
+    hi = 1.0 if k == n else min(1.0, c + h)
+    return (lo, hi)
 
 
 def compare_ler(B: "mbbp.Bases", L: "mbbp.Logicals", w, g, p: float, shots: int, iters: int,
