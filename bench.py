@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bb144", choices=["bb144", "mixed", "learned", "paper", "wms"],
+    ap.add_argument("--workload", default="bb144", choices=["bb144", "mixed", "learned", "paper", "wms", "gb882"],
                     help="bb144: the headline configuration; mixed: [[72]]/[[144]]/[[288]] in one "
                          "persistent graph-captured launch vs plain per-code launches")
     ap.add_argument("--shots", type=int, default=None,
@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="bb144: skip the mixed-batch and length-882 legs reported beside the headline")
     ap.add_argument("--train-steps", type=int, default=100, help="learned: training steps")
+    ap.add_argument("--p", type=float, default=None, help="gb882: a single error rate")
+    ap.add_argument("--wms", action="store_true", help="gb882: also the weighted decoder at its initial weights")
     ap.add_argument("--train-batch", type=int, default=512, help="learned: shots per training step")
     return ap.parse_args()
 
@@ -386,10 +388,13 @@ def run_mixed(args):
 GB882_P = (0.02, 0.03, 0.04, 0.05, 0.06)
 
 
-def gb882_measure(shots: int, steps: int = 1, warmup: int = 1):
+def gb882_measure(shots: int, steps: int = 1, warmup: int = 1, p_list=None, wms: bool = False):
     """Plain MBBP-LD on the length-882 GB code (R = 64, 100 iterations,
     depolarizing p in {0.02 .. 0.06}, X errors decoded with H_Z): shots/s per
-    p from CUDA events around each decode call (BP + FWS), inputs resident."""
+    p from CUDA events around each decode call (BP + FWS), inputs resident.
+    With `wms`, also the learned-form decoder (mbbp_wms_decode, T = 25) with
+    its initial weights w = alpha, g = 0, which decide exactly as plain
+    MBBP-LD: the same work through the weighted kernel."""
     import torch
 
     from paper_2605_14170_gb300 import mbbp
@@ -406,7 +411,8 @@ def gb882_measure(shots: int, steps: int = 1, warmup: int = 1):
     syn = torch.empty((shots, B.m), dtype=torch.uint8, device=dev)
     out = None
     per_p = {}
-    for ip, p in enumerate(GB882_P):
+    p_list = GB882_P if p_list is None else p_list
+    for ip, p in enumerate(p_list):
         mbbp.mbbp_sample_errors(n, shots, 90_000_000_000 + ip * shots, SEED, p, mbbp.NOISE_DEPOLARIZING, ex, ez)
         mbbp.mbbp_syndrome(B, ex, syn)
         pm = 2 * p / 3
@@ -427,11 +433,40 @@ def gb882_measure(shots: int, steps: int = 1, warmup: int = 1):
         it = (out["iters"].to(torch.int64) & 0xFFFF).float().mean().item()
         per_p[str(p)] = {"shots_per_s": shots / (ms / 1e3), "decode_ms": ms, "mean_K": it,
                          "success": float(out["success"].float().mean().item())}
+        if wms:
+            w, g = mbbp.wms_params(B, 25, alpha=ALPHA, device=dev)
+            o2 = {k: torch.empty_like(v) for k, v in out.items()}
+            wt = []
+            for k in range(warmup + steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                mbbp.mbbp_wms_decode(B, syn, llr, ITERS, 25, w, g, o2["e_hat"], o2["conv"], o2["success"],
+                                     o2["workspace"], iters_run=o2["iters"], selected=o2["selected"])
+                e1.record()
+                e1.synchronize()
+                if k >= warmup:
+                    wt.append(e0.elapsed_time(e1))
+            wms_ms = statistics.mean(wt)
+            per_p[str(p)]["wms_decode_ms"] = wms_ms
+            per_p[str(p)]["wms_shots_per_s"] = shots / (wms_ms / 1e3)
+            per_p[str(p)]["wms_identical_to_plain"] = bool(torch.equal(o2["e_hat"], out["e_hat"]))
     total_ms = sum(v["decode_ms"] for v in per_p.values())
     return {"workload": "length-882 GB code (seeded, k=4), R=64, 100 iters, alpha 0.625, flooding, FWS, "
                         "depolarizing X errors", "shots_per_p": shots, "steps": steps, "warmup": warmup,
-            "shots_per_s": len(GB882_P) * shots / (total_ms / 1e3), "per_p": per_p,
+            "shots_per_s": len(p_list) * shots / (total_ms / 1e3), "per_p": per_p,
             "bases_build_s": build_s}
+
+
+def run_gb882(args):
+    """Plain MBBP-LD on the length-882 GB code as its own JSON line (`--p`
+    picks one p; default all five)."""
+    r = gb882_measure(args.shots, args.steps, args.warmup, None if args.p is None else (args.p,), wms=args.wms)
+    ms = sum(v["decode_ms"] for v in r["per_p"].values())
+    line = {"metric": "decoded shots/s", "value": r["shots_per_s"], "unit": "shots/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": r["workload"], "shots_per_p": args.shots}, "per_p": r["per_p"]}
+    print(json.dumps(line), flush=True)
 
 
 def run_learned(args):
@@ -697,7 +732,8 @@ def run_wms(args):
 def main():
     args = parse()
     if args.shots is None:
-        args.shots = {"mixed": 300_000, "learned": 100_000, "paper": 200_000}.get(args.workload, 1_000_000)
+        args.shots = {"mixed": 300_000, "learned": 100_000, "paper": 200_000, "gb882": 100_000}.get(args.workload,
+                                                                                                   1_000_000)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -712,6 +748,9 @@ def main():
         return
     if args.workload == "wms":
         run_wms(args)
+        return
+    if args.workload == "gb882":
+        run_gb882(args)
         return
 
     import torch

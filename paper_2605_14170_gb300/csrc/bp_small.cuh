@@ -111,12 +111,14 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
 // (|q| <= |mu| + 6 LMAX).
 //
 // The update runs for the 32 lanes of a variable step at once: DM is the largest
-// degree among the step's lanes (warp-uniform), and a lane of degree
-// deg <= DM runs the same instructions with its edges i >= deg predicated
-// off, which loads, adds and stores nothing for it.  Each lane's sums are
-// therefore those of its own degree (same terms, same order), while the step
-// issues one load and one store instruction per edge position instead of one
-// per degree case present among its lanes.
+// degree among the step's lanes (warp-uniform).  A lane of degree deg < DM
+// loads nothing for its edges i >= deg and takes them as +0.0, which leaves
+// every sum unchanged (x + 0 = x exactly for every x but -0, and no sum here
+// is -0: they start from mu + 0 and a sum that cancels rounds to +0); it
+// stores only its own deg messages.  Each lane's sums are therefore those of
+// its own degree (same terms, same order, exact), while the step issues one
+// load and one store instruction per edge position instead of one per
+// degree case present among its lanes.
 template <int DM>
 __device__ __forceinline__ float var_upd_step(char* smc, const uint4& d, float mu, int deg) {
     uint32_t a[DM];
@@ -125,19 +127,16 @@ __device__ __forceinline__ float var_upd_step(char* smc, const uint4& d, float m
     for (int i = 0; i < DM; ++i) a[i] = addr_of(d, i);
 #pragma unroll
     for (int i = 0; i < DM; ++i) m[i] = (i < deg) ? lds(smc, a[i]) : 0.0f;
-    float P[DM + 1];  // P[i] = mu + m_0 + ... + m_{min(i, deg)-1}
+    float P[DM + 1];
     P[0] = mu;
 #pragma unroll
-    for (int i = 0; i < DM; ++i) P[i + 1] = (i < deg) ? __fadd_rn(P[i], m[i]) : P[i];
+    for (int i = 0; i < DM; ++i) P[i + 1] = __fadd_rn(P[i], m[i]);
 #pragma unroll
     for (int i = 0; i < DM; ++i) {
-        if (i < deg) {
-            float q = P[i];
+        float q = P[i];
 #pragma unroll
-            for (int t = i + 1; t < DM; ++t)
-                if (t < deg) q = __fadd_rn(q, m[t]);
-            sts(smc, a[i], q);
-        }
+        for (int t = i + 1; t < DM; ++t) q = __fadd_rn(q, m[t]);
+        if (i < deg) sts(smc, a[i], q);
     }
     return P[DM];
 }

@@ -52,10 +52,44 @@ __host__ __device__ inline WmsLayout wms_layout(int DC, int MP, int n, int ckpt)
 // Each step's descriptor is loaded one step ahead; a variable's slots and
 // messages are read once into registers (at most DV of them).
 template <int DV>
-__device__ __forceinline__ void wms_var_pass(const DevBases& B, const uint2* vd, const float* m,
+__device__ __forceinline__ void wms_var_pass(const DevBases& B, int b, const uint2* vd, const float* m,
                                              float* q, const float* mu, float* post) {
     const int lane = threadIdx.x & 31;
     const int n = B.n;
+    if constexpr (DV == 6) {
+        // width 6: the slots come packed in the descriptor (vdesc6), no
+        // slot-list load; byte offsets index m and q alike (same layout)
+        const uint4* vd6 = B.vdesc6 + (size_t)b * n;
+        uint4 dn = (lane < n) ? __ldg(vd6 + lane) : make_uint4(0u, 0u, 0u, 0u);
+        for (int p = lane; p < n; p += 32) {
+            const uint4 d = dn;
+            if (p + 32 < n) dn = __ldg(vd6 + p + 32);
+            const int v = d.x & 0xffff, deg = (int)(d.x >> 16);
+            uint32_t s[6];
+            float mv[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                s[i] = (i < deg) ? generic_bp::packed_off(d, i) : 0u;
+                mv[i] = (i < deg) ? generic_bp::msg_at(const_cast<float*>(m), s[i]) : 0.0f;
+            }
+            float acc = mu[v];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                if (i < deg) acc = __fadd_rn(acc, mv[i]);
+            if (post) post[v] = acc;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                if (i < deg) {
+                    float x = mu[v];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+                        if (k < deg && k != i) x = __fadd_rn(x, mv[k]);
+                    generic_bp::msg_at(q, s[i]) = x;
+                }
+            }
+        }
+        return;
+    }
     uint2 dn = (lane < n) ? __ldg(vd + lane) : make_uint2(0u, 0u);
     for (int p = lane; p < n; p += 32) {
         const uint2 d = dn;
@@ -104,19 +138,27 @@ __device__ __forceinline__ void wms_check_pass(const DevBases& B, int b, const u
         float qq[DC];
 #pragma unroll
         for (int j = 0; j < DC; ++j) qq[j] = (j < deg) ? q[j * MP + r] : MBBP_LMAX;
-        const uint32_t s = (sb >> k) & 1u;
+        // the min over the other edges (and LMAX) from prefix and suffix
+        // minima, the sign parity from the sign bits (no q is -0: the LLRs
+        // enter as mu + 0), both exact
+        uint32_t sx = ((sb >> k) & 1u) << 31;
+#pragma unroll
+        for (int j = 0; j < DC; ++j) sx ^= __float_as_uint(qq[j]);
+        sx &= 0x80000000u;
+        float pre[DC], suf[DC];
+        pre[0] = MBBP_LMAX;
+#pragma unroll
+        for (int j = 1; j < DC; ++j) pre[j] = fminf(pre[j - 1], fabsf(qq[j - 1]));
+        suf[DC - 1] = MBBP_LMAX;
+#pragma unroll
+        for (int j = DC - 2; j >= 0; --j)
+            suf[j] = (j == DC - 2) ? fabsf(qq[DC - 1]) : fminf(suf[j + 1], fabsf(qq[j + 1]));
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
             if (j >= deg) continue;
-            float mn = MBBP_LMAX;
-            uint32_t neg = s;
-#pragma unroll
-            for (int t = 0; t < DC; ++t) {
-                if (t == j || t >= deg) continue;
-                mn = fminf(mn, fabsf(qq[t]));
-                neg ^= (qq[t] < 0.f) ? 1u : 0u;
-            }
-            const float c = __fmul_rn(__ldg(wt + e0 + j), neg ? -mn : mn);
+            const float mn = (j == DC - 1) ? pre[j] : (j == 0 ? fminf(MBBP_LMAX, suf[0]) : fminf(pre[j], suf[j]));
+            const float smn = __uint_as_float(__float_as_uint(mn) ^ ((sx ^ __float_as_uint(qq[j])) & 0x80000000u));
+            const float c = __fmul_rn(__ldg(wt + e0 + j), smn);
             const float gg = __ldg(gt + e0 + j);
             const float mo = m[j * MP + r];
             m[j * MP + r] = __fadd_rn(__fmul_rn(gg, mo), __fmul_rn(__fsub_rn(1.0f, gg), c));
@@ -144,20 +186,31 @@ wms_forward_kernel(const WmsArgs a) {
     float* post = mu + L.npad;
     uint8_t* eh = reinterpret_cast<uint8_t*>(post + L.npad);
     const int orow_steps = B.mpad >> 5;
+    // H's columns for the halting test, once per block
+    uint16_t* hcol_s = reinterpret_cast<uint16_t*>(smem + (blockDim.x >> 5) * L.fwd_bytes);
+    if (a.decode) {
+        for (int i = threadIdx.x; i < DC * B.mpad; i += blockDim.x) hcol_s[i] = __ldg(B.hcol + i);
+        __syncthreads();
+    }
+    // work items representation-major (g = b * batch + shot): the warps
+    // resident at one time share a representation's tables in L1; outputs
+    // stay indexed by item = shot * R + b
+    const unsigned long long batch = a.total_items / (unsigned long long)R;
     for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(a.counter, 1ull);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= a.total_items) break;
-        const int shot = (int)(item / (unsigned long long)R);
-        const int b = (int)(item - (unsigned long long)shot * R);
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(a.counter, 1ull);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= a.total_items) break;
+        const int b = (int)(g / batch);
+        const int shot = (int)(g - (unsigned long long)b * batch);
+        const unsigned long long item = (unsigned long long)shot * R + b;
         const uint32_t* rinfo = B.rowinfo + (size_t)b * MP;
         const uint2* vd = B.vdesc + (size_t)b * n;
         const int Mb = __ldg(B.rows + b);
         const float* llr = a.llr + (size_t)shot * a.llr_stride;
         const uint8_t* sy = a.synd + (size_t)shot * m_rows;
         for (int v = lane; v < n; v += 32) {
-            const float x = __ldg(llr + v);
+            const float x = __fadd_rn(__ldg(llr + v), 0.0f);  // -0 -> +0 (sign bits decide the check rule)
             mu[v] = x;
             post[v] = x;
             eh[v] = (x < 0.f) ? 1 : 0;
@@ -188,7 +241,7 @@ wms_forward_kernel(const WmsArgs a) {
                     if (r < m_rows) {
                         uint32_t par = (sb >> k) & 1u;
 #pragma unroll
-                        for (int j = 0; j < DC; ++j) par ^= eh[__ldg(B.hcol + j * B.mpad + r)];
+                        for (int j = 0; j < DC; ++j) par ^= eh[hcol_s[j * B.mpad + r]];
                         ok = ok && (par == 0u);
                     }
                 }
@@ -207,7 +260,7 @@ wms_forward_kernel(const WmsArgs a) {
             const float* gt = a.g + ((size_t)b * a.T + tp) * a.E;
             wms_check_pass<DC>(B, b, rinfo, Mb, sb, q, m, wt, gt);
             __syncwarp();
-            wms_var_pass<DV>(B, vd, m, q, mu, post);
+            wms_var_pass<DV>(B, b, vd, m, q, mu, post);
             __syncwarp();
             if (a.decode) {
                 for (int v = lane; v < n; v += 32) eh[v] = (post[v] < 0.f) ? 1 : 0;
@@ -286,7 +339,7 @@ wms_backward_kernel(const WmsArgs a) {
         const int Mb = __ldg(B.rows + b);
         const float* llr = a.llr + (size_t)shot * a.llr_stride;
         const uint8_t* sy = a.synd + (size_t)shot * m_rows;
-        for (int v = lane; v < n; v += 32) mu[v] = __ldg(llr + v);
+        for (int v = lane; v < n; v += 32) mu[v] = __fadd_rn(__ldg(llr + v), 0.0f);  // as the forward pass
         uint32_t sb = 0;
         for (int k = 0; k < (MP >> 5); ++k) {
             const int r = lane + 32 * k;
@@ -329,7 +382,7 @@ wms_backward_kernel(const WmsArgs a) {
                         for (int i = 0; i < deg; ++i) q[__ldg(B.vslot + d.x + i)] = mu[v];
                     }
                 } else {
-                    wms_var_pass<DV>(B, vd, mprev, q, mu, nullptr);
+                    wms_var_pass<DV>(B, b, vd, mprev, q, mu, nullptr);
                 }
                 for (int i = lane; i < L.S; i += 32) mcur[i] = mprev[i];
                 __syncwarp();
@@ -348,7 +401,7 @@ wms_backward_kernel(const WmsArgs a) {
                         for (int i = 0; i < deg; ++i) q[__ldg(B.vslot + d.x + i)] = mu[v];
                     }
                 } else {
-                    wms_var_pass<DV>(B, vd, mprev, q, mu, nullptr);
+                    wms_var_pass<DV>(B, b, vd, mprev, q, mu, nullptr);
                 }
                 for (int i = lane; i < L.S; i += 32) gq[i] = 0.0f;
                 __syncwarp();
@@ -462,15 +515,17 @@ cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm
     const bool smem_st = backward && (size_t)kWmsStateWarps * (L.bwd_bytes + st_bytes) <= 110 * 1024;
     const size_t per_warp = backward ? L.bwd_bytes + (smem_st ? st_bytes : 0) : L.fwd_bytes;
     if (per_warp > 200 * 1024) return cudaErrorInvalidConfiguration;
+    // the forward kernel also holds H's columns once per block (halting test)
+    const size_t fixed = backward ? 0 : (size_t)((K * a.B.mpad * 2 + 15) & ~15);
     const void* kern = !backward ? reinterpret_cast<const void*>(wms_forward_kernel<K, K>)
                        : smem_st ? reinterpret_cast<const void*>(wms_backward_kernel<K, K, true>)
                                  : reinterpret_cast<const void*>(wms_backward_kernel<K, K, false>);
     // the block size with the most resident warps per SM (ties: the smaller
     // block), within 200 KB of shared memory per block
     int warps = 0, per_sm = 0;
-    for (int w = 1; w <= kWmsWarps && (size_t)w * per_warp <= 200 * 1024; ++w) {
+    for (int w = 1; w <= kWmsWarps && fixed + (size_t)w * per_warp <= 200 * 1024; ++w) {
         int b = 0;
-        cudaError_t e = prepare_kernel(kern, w * 32, (size_t)w * per_warp, &b);
+        cudaError_t e = prepare_kernel(kern, w * 32, fixed + (size_t)w * per_warp, &b);
         if (e != cudaSuccess) return e;
         if (b * w > per_sm * warps) {
             warps = w;
@@ -478,7 +533,7 @@ cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm
         }
     }
     if (warps == 0) return cudaErrorInvalidConfiguration;
-    const size_t smem = warps * per_warp;
+    const size_t smem = fixed + warps * per_warp;
     unsigned long long want = (a.total_items + warps - 1) / warps;
     unsigned long long grid = (unsigned long long)per_sm * sm_count;
     if (want < grid) grid = want;
