@@ -213,6 +213,37 @@ __device__ __forceinline__ float var_dispatch_packed(int deg, float* msg, const 
 }
 
 
+// A "group" of G warps decodes one item together (G = 1: one warp).  Its
+// threads synchronise on named barrier `bar` (bar.sync / bar.red with the
+// group's thread count), which only its own 32 G threads use.
+template <int G>
+__device__ __forceinline__ void gsync(int bar) {
+    if constexpr (G == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(32 * G) : "memory");
+    }
+}
+
+// AND of p over the group's threads (all of them must call it).
+template <int G>
+__device__ __forceinline__ bool gall(bool p, int bar) {
+    if constexpr (G == 1) {
+        return __all_sync(kFull, p);
+    } else {
+        uint32_t r;
+        asm volatile(
+            "{\n\t.reg .pred pi, po;\n\t"
+            "setp.ne.u32 pi, %1, 0;\n\t"
+            "bar.red.and.pred po, %2, %3, pi;\n\t"
+            "selp.u32 %0, 1, 0, po;\n\t}"
+            : "=r"(r)
+            : "r"((uint32_t)p), "r"(bar), "r"(32 * G)
+            : "memory");
+        return r != 0;
+    }
+}
+
 // Bit-pack the hard decision eh[0..n) into the candidate words of `item`,
 // and store the convergence flag and iteration count.
 __device__ __forceinline__ void store_item(const ShotIO& io, unsigned long long item, int n, int W,
@@ -235,21 +266,43 @@ __device__ __forceinline__ void store_item(const ShotIO& io, unsigned long long 
     }
 }
 
-// Decode one (shot, representation) item.  area: this warp's shared-memory
-// area (warp_layout(DC, ...).per_warp bytes); hcol: columns of the rows of H
-// ([DC][mpad], shared or global memory).  TRACE: io.c2v receives the check
-// messages of every iteration (the last one run remains).
-template <int DC, int DV, int RULE, bool TRACE = false>
-__device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, int shot, int b,
-                                         unsigned char* area, const uint16_t* hcol) {
+// store_item for a group of G > 1 warps: warp wig of the group packs the
+// words wig, wig + G, ...
+template <int G>
+__device__ __forceinline__ void store_item_group(const ShotIO& io, unsigned long long item, int n, int W,
+                                                 const uint8_t* eh, bool conv, int K, int wig) {
     const int lane = threadIdx.x & 31;
+    for (int w = wig; w < W; w += G) {
+        const int v = 32 * w + lane;
+        const uint32_t word = __ballot_sync(kFull, v < n && eh[v]);
+        if (lane == 0) io.cand[item * W + w] = word;
+    }
+    if (wig == 0 && lane == 0) {
+        io.conv[item] = conv ? 1 : 0;
+        if (io.iters_run) io.iters_run[item] = (uint16_t)K;
+    }
+}
+
+// Decode one (shot, representation) item.  area: the shared-memory area of
+// the warp (G = 1) or group of G warps that decodes it (warp_layout(DC,
+// ...).per_warp bytes); hcol: columns of the rows of H ([DC][mpad], shared
+// or global memory).  A group's threads own rows gt, gt + 32 G, ... and
+// variable positions likewise (gt: the thread's index in the group) and meet
+// on named barrier `bar` between passes; the arithmetic of every row and
+// variable is the same whatever G.  TRACE: io.c2v receives the check
+// messages of every iteration (the last one run remains).
+template <int DC, int DV, int RULE, bool TRACE = false, int G = 1>
+__device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, int shot, int b,
+                                         unsigned char* area, const uint16_t* hcol, int bar = 0) {
+    constexpr int GT = 32 * G;
+    const int lane = (int)(threadIdx.x % GT);  // the thread's index in its group
     const int MP = B.MP, n = B.n, m = B.m, R = B.R, W = B.W, mpad = B.mpad;
     const WarpLayout L = warp_layout(DC, MP, mpad, n);
     float* msg = reinterpret_cast<float*>(area);
     float* mu_s = msg + L.S;
     uint8_t* eh = reinterpret_cast<uint8_t*>(mu_s + L.npad);
-    const int row_steps = MP >> 5;
-    const int orow_steps = mpad >> 5;
+    const int row_steps = (MP + GT - 1) / GT;
+    const int orow_steps = (mpad + GT - 1) / GT;
     const unsigned long long item = (unsigned long long)shot * R + b;
     const uint32_t* rinfo = B.rowinfo + (size_t)b * MP;
     const uint2* vd = B.vdesc + (size_t)b * n;
@@ -257,9 +310,9 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
     const float* llr = io.llr + (size_t)shot * io.llr_stride;
     const uint8_t* sy = io.synd + (size_t)shot * m;
 
-    __syncwarp();
+    gsync<G>(bar);
     // channel LLRs, hard decision of the LLRs, syndrome bits of my rows
-    for (int v = lane; v < n; v += 32) {
+    for (int v = lane; v < n; v += GT) {
         const float x = __ldg(llr + v);
         mu_s[v] = __fadd_rn(x, 0.0f);  // -0 -> +0 (sign bits decide the check rule)
         eh[v] = (x < 0.f) ? 1 : 0;
@@ -267,14 +320,14 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
     if (lane == 0) eh[n] = 0;  // padding column of hcol
     uint32_t sb = 0;
     for (int k = 0; k < row_steps; ++k) {
-        const int r = lane + 32 * k;
+        const int r = lane + GT * k;
         if (r < Mb) sb |= (uint32_t)(__ldg(sy + (__ldg(rinfo + r) & 0xffffu)) & 1u) << k;
     }
-    __syncwarp();
+    gsync<G>(bar);
     // q^(0)_{v->c} = mu_v
     if constexpr (DC == 6) {
         const uint4* vd6 = B.vdesc6 + (size_t)b * n;
-        for (int p = lane; p < n; p += 32) {
+        for (int p = lane; p < n; p += GT) {
             const uint4 d = __ldg(vd6 + p);
             const int v = d.x & 0xffff, deg = (int)(d.x >> 16);
             const float x = mu_s[v];
@@ -284,7 +337,7 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
             if (io.post) io.post[item * n + v] = x;
         }
     } else {
-        for (int p = lane; p < n; p += 32) {
+        for (int p = lane; p < n; p += GT) {
             const uint2 d = __ldg(vd + p);
             const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
             const float x = mu_s[v];
@@ -292,7 +345,7 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
             if (io.post) io.post[item * n + v] = x;
         }
     }
-    __syncwarp();
+    gsync<G>(bar);
 
     int K = 0;
     bool conv = false;
@@ -302,19 +355,19 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
         // other groups are tested only if it passed
         bool ok = true;
         for (int k = 0; k < orow_steps; ++k) {
-            const int r = lane + 32 * k;
+            const int r = lane + GT * k;
             if (r < m) {
                 uint32_t par = (sb >> k) & 1u;
 #pragma unroll
                 for (int j = 0; j < DC; ++j) par ^= eh[hcol[j * mpad + r]];
                 ok = ok && (par == 0u);
             }
-            if (k == 0 && orow_steps > 1) {  // warp-uniform condition
-                const bool first_ok = __all_sync(kFull, ok);
+            if (k == 0 && orow_steps > 1) {  // group-uniform condition
+                const bool first_ok = gall<G>(ok, bar);
                 if (!first_ok) break;
             }
         }
-        if (__all_sync(kFull, ok)) {
+        if (gall<G>(ok, bar)) {
             conv = true;
             K = it;
             break;
@@ -325,7 +378,7 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
         }
         // check pass
         for (int k = 0; k < row_steps; ++k) {
-            const int r = lane + 32 * k;
+            const int r = lane + GT * k;
             if (r < Mb) {
                 const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
                 float* tr = TRACE ? io.c2v + item * (unsigned long long)io.c2v_stride +
@@ -334,16 +387,16 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
                 check_row<DC, RULE>(msg, r, MP, deg, (sb >> k) & 1u, io.alpha, tr);
             }
         }
-        __syncwarp();
+        gsync<G>(bar);
         // variable pass, posterior, hard decision; each step's descriptor is
         // loaded one step ahead (width 6: with the slots packed in, so no load
         // of the pass waits on L1; other widths: the slot list still does)
         if constexpr (DC == 6) {
             const uint4* vd6 = B.vdesc6 + (size_t)b * n;
             uint4 dn = (lane < n) ? __ldg(vd6 + lane) : make_uint4(0u, 0u, 0u, 0u);
-            for (int p = lane; p < n; p += 32) {
+            for (int p = lane; p < n; p += GT) {
                 const uint4 d = dn;
-                if (p + 32 < n) dn = __ldg(vd6 + p + 32);
+                if (p + GT < n) dn = __ldg(vd6 + p + GT);
                 const int v = d.x & 0xffff, deg = (int)(d.x >> 16);
                 const float post = var_dispatch_packed(deg, msg, d, mu_s[v]);
                 eh[v] = (post < 0.f) ? 1 : 0;
@@ -351,20 +404,23 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
             }
         } else {
             uint2 dn = (lane < n) ? __ldg(vd + lane) : make_uint2(0u, 0u);
-            for (int p = lane; p < n; p += 32) {
+            for (int p = lane; p < n; p += GT) {
                 const uint2 d = dn;
-                if (p + 32 < n) dn = __ldg(vd + p + 32);
+                if (p + GT < n) dn = __ldg(vd + p + GT);
                 const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
                 const float post = var_dispatch<1, DV>(deg, msg, B.vslot + d.x, mu_s[v]);
                 eh[v] = (post < 0.f) ? 1 : 0;
                 if (io.post) io.post[item * n + v] = post;
             }
         }
-        __syncwarp();
+        gsync<G>(bar);
     }
     // candidate e_t (bit-packed), convergence flag, iterations
-    store_item(io, item, n, W, eh, conv, K);
-    __syncwarp();
+    if constexpr (G == 1)
+        store_item(io, item, n, W, eh, conv, K);
+    else
+        store_item_group<G>(io, item, n, W, eh, conv, K, lane >> 5);
+    gsync<G>(bar);
 }
 
 // Per-warp shared memory of the serial schedule: the flooding layout plus

@@ -29,17 +29,23 @@ void* g_scratch_addr[kMaxDevices] = {};
 // several small ones.  Each class is compiled for its own block size.
 constexpr int kGenericWideWarps = 16;
 
-template <int DC, int DV, int RULE, int MAXW, bool TRACE = false>
+// G warps decode each item together (G = 1: one warp per item; G = 2 for
+// codes whose per-item shared memory, not registers, limits the resident
+// warps: the same shared memory then holds twice the warps).  Group g of the
+// block uses named barrier 1 + g.
+template <int DC, int DV, int RULE, int MAXW, bool TRACE = false, int G = 1>
 __global__ void __launch_bounds__(MAXW * 32)
 decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long group_item[MAXW];
     const DevBases& B = a.B;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int R = B.R;
+    const int grp = (int)(threadIdx.x >> 5) / G;
+    const int gt = (int)(threadIdx.x % (32 * G));
+    const int bar = 1 + grp;
     const generic_bp::WarpLayout L = generic_bp::warp_layout(DC, B.MP, B.mpad, B.n);
     uint16_t* hcol_s = reinterpret_cast<uint16_t*>(smem);
-    unsigned char* area = smem + L.hcol_bytes + warp * L.per_warp;
+    unsigned char* area = smem + L.hcol_bytes + grp * L.per_warp;
     for (int i = threadIdx.x; i < DC * B.mpad; i += blockDim.x) hcol_s[i] = __ldg(B.hcol + i);
     __syncthreads();
     // Work items are taken representation-major (item = b * batch + shot):
@@ -48,14 +54,21 @@ decode_kernel(const DecodeArgs a) {
     const unsigned long long batch = (unsigned long long)a.io.batch;
     for (;;) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(a.counter, 1ull);
-        item = __shfl_sync(kFull, item, 0);
+        if constexpr (G == 1) {
+            if (lane == 0) item = atomicAdd(a.counter, 1ull);
+            item = __shfl_sync(kFull, item, 0);
+        } else {
+            // the group's first thread takes the item; the slot is rewritten
+            // only after the item's last barrier, which every reader passed
+            if (gt == 0) group_item[grp] = atomicAdd(a.counter, 1ull);
+            generic_bp::gsync<G>(bar);
+            item = group_item[grp];
+        }
         if (item >= a.total_items) break;
         const int b = (int)(item / batch);
         const int shot = (int)(item - (unsigned long long)b * batch);
-        generic_bp::run_item<DC, DV, RULE, TRACE>(B, a.io, shot, b, area, hcol_s);
+        generic_bp::run_item<DC, DV, RULE, TRACE, G>(B, a.io, shot, b, area, hcol_s, bar);
     }
-    (void)R;
 }
 
 // The serial-schedule kernel: same work list as decode_kernel, one warp per
@@ -223,37 +236,55 @@ cudaError_t launch_serial_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
 
 template <int K, int RULE, bool TRACE>
 cudaError_t launch_decode_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
-    const void* narrow = reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE>);
-    const void* wide = reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps, TRACE>);
+    // Launch shapes: (block class, warps per item G).  The narrow class runs
+    // blocks of up to 8 warps, the wide class up to 16 (compiled for
+    // 512-thread blocks, it takes more registers).  For each shape, the
+    // block size with the most resident warps per SM (ties: the smaller
+    // block) within 200 KB of shared memory per block; a block holds H's
+    // columns once plus one message area per item.  G = 2 is taken when it
+    // holds at least half again as many warps as G = 1 (codes whose message
+    // areas, not registers, limit the resident warps); among G = 1 shapes
+    // the wide class only when it holds at least a quarter more warps.
+    const void* kerns[2][2] = {
+        {reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 1>),
+         reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 1>)},
+        {reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 2>),
+         reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 2>)}};
     const generic_bp::WarpLayout L = generic_bp::warp_layout(K, a.B.MP, a.B.mpad, a.B.n);
-    // per class, the block size with the most resident warps per SM (ties:
-    // the smaller block) within 200 KB of shared memory per block; the wide
-    // class only when it holds at least a quarter more warps (its code,
-    // compiled for 512-thread blocks, takes more registers)
-    int choice[2][2] = {{0, 0}, {0, 0}};  // [class] = {warps per block, blocks per SM}
-    for (int w = 1; w <= kGenericWideWarps; ++w) {
-        const size_t sm_w = (size_t)L.hcol_bytes + (size_t)w * L.per_warp;
-        if (sm_w > 200 * 1024) break;
-        const int cls = w <= kWarpsPerBlock ? 0 : 1;
-        int b = 0;
-        cudaError_t e = prepare_kernel(cls == 0 ? narrow : wide, w * 32, sm_w, &b);
-        if (e != cudaSuccess) return e;
-        if (b * w > choice[cls][0] * choice[cls][1]) {
-            choice[cls][0] = w;
-            choice[cls][1] = b;
+    int choice[2][2][2] = {};  // [G-1][class] = {warps per block, blocks per SM}
+    for (int gi = 0; gi < 2; ++gi) {
+        const int G = gi + 1;
+        for (int w = G; w <= kGenericWideWarps; w += G) {
+            const size_t sm_w = (size_t)L.hcol_bytes + (size_t)(w / G) * L.per_warp;
+            if (sm_w > 200 * 1024) break;
+            const int cls = w <= kWarpsPerBlock ? 0 : 1;
+            int b = 0;
+            cudaError_t e = prepare_kernel(kerns[gi][cls], w * 32, sm_w, &b);
+            if (e != cudaSuccess) return e;
+            if (b * w > choice[gi][cls][0] * choice[gi][cls][1]) {
+                choice[gi][cls][0] = w;
+                choice[gi][cls][1] = b;
+            }
         }
     }
-    const bool use_wide = choice[1][0] > 0 && 4 * choice[1][0] * choice[1][1] >= 5 * choice[0][0] * choice[0][1];
-    const int warps = choice[use_wide][0], per_sm = choice[use_wide][1];
+    auto resident = [&](int gi, int cls) { return choice[gi][cls][0] * choice[gi][cls][1]; };
+    const int best1 = resident(0, 1) * 4 >= resident(0, 0) * 5 ? 1 : 0;
+    const int best2 = resident(1, 1) > resident(1, 0) ? 1 : 0;
+    const bool use_g2 = 2 * resident(1, best2) >= 3 * resident(0, best1);
+    const int gi = use_g2 ? 1 : 0, cls = use_g2 ? best2 : best1;
+    const int warps = choice[gi][cls][0], per_sm = choice[gi][cls][1];
     if (warps == 0) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)L.hcol_bytes + (size_t)warps * L.per_warp;
-    unsigned long long want = (a.total_items + warps - 1) / warps;
+    const int G = gi + 1;
+    const size_t smem = (size_t)L.hcol_bytes + (size_t)(warps / G) * L.per_warp;
+    const unsigned long long groups = (unsigned long long)(warps / G);
+    unsigned long long want = (a.total_items + groups - 1) / groups;
     unsigned long long grid = (unsigned long long)per_sm * (unsigned long long)sm_count;
     if (want < grid) grid = want;
-    if (use_wide)
-        decode_kernel<K, K, RULE, kGenericWideWarps, TRACE><<<(unsigned)grid, warps * 32, smem, s>>>(a);
-    else
-        decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    const dim3 gd((unsigned)grid), bd((unsigned)(warps * 32));
+    if (gi == 0 && cls == 0) decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 1><<<gd, bd, smem, s>>>(a);
+    if (gi == 0 && cls == 1) decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 1><<<gd, bd, smem, s>>>(a);
+    if (gi == 1 && cls == 0) decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 2><<<gd, bd, smem, s>>>(a);
+    if (gi == 1 && cls == 1) decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 2><<<gd, bd, smem, s>>>(a);
     return cudaGetLastError();
 }
 

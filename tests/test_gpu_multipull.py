@@ -149,3 +149,22 @@ def test_mixed_launches_many_items_per_warp(M):
         for key, rkey in (("conv", "conv"), ("iters", "iters"), ("selected", "selected"),
                           ("success", "success"), ("e_hat", "ehat")):
             assert np.array_equal(got[key], ref[rkey]), (name, key)
+
+
+def test_generic_kernel_length_882_many_items_per_group(M):
+    """The generic flooding kernel on the length-882 GB code with R = 64
+    (its largest workload: rows of H^(t) up to 617, where two warps share
+    each item's message area) on 320 shots: 20,480 (shot, representation)
+    items, at least twice the resident-warp bound, every output equal to the
+    FP32 oracle's."""
+    shots, R, p = 320, 64, 0.04
+    H = named_code("gb882").HZ
+    ex, _ = oracle.sample(SEED + 5, 0, shots, 882, p, "depolarizing")
+    s = oracle.syndrome(H, ex)
+    B = M.mbbp_build_bases(H, R, SEED)
+    items, bound = shots * R, resident_warp_bound()
+    assert items >= 2 * bound, (items, bound)
+    llr = channel_llr(882, 2 * p / 3).astype(np.float32)
+    got = _decode(M, B, s, llr, 100, 0.625)
+    ref = oracle_decode_parallel(H, B.sets, s, llr, 100, 0.625)
+    _assert_exact(got, ref, "gb882")
