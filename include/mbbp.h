@@ -351,7 +351,8 @@ mbbp_status mbbp_plan_info(const mbbp_plan* P, int32_t* warps, int32_t* chunk, i
 
 /* Workspace of mbbp_wms_forward / mbbp_wms_backward: the checkpoints of m,
  * one every `ckpt` iterations ((T-1)/ckpt of them per (shot, representation)),
- * and the recomputed states of one segment per warp of the backward grid. */
+ * and, for codes whose segment states do not fit in shared memory, the
+ * recomputed states of one segment per warp of the backward grid. */
 size_t mbbp_wms_workspace_size(const mbbp_bases* B, int batch, int T, int ckpt);
 
 /* Forward pass.  syndromes, llr, llr_stride: as mbbp_decode.  etrue: device

@@ -10,7 +10,8 @@
 // work items (code, chunk of shots, representation) from the launch's
 // counter, in the order the plan chose (heaviest codes first by default).
 // Every per-code argument travels in the kernel parameters, so a captured
-// CUDA graph holds them by value.
+// CUDA graph holds them by value.  Within a code, items are taken
+// representation-major.
 #include "bp_generic.cuh"
 #include "bp_small.cuh"
 
@@ -32,10 +33,13 @@ __device__ __forceinline__ bool next_item(const MixedArgs& a, MixedItem& it) {
     while (c + 1 < a.n_codes && g >= a.codes[c + 1].first) ++c;
     const MixedCode& mc = a.codes[c];
     const unsigned long long l = g - mc.first;
-    const int R = mc.B.R;
-    const int sblock = (int)(l / (unsigned long long)R);
+    // representation-major within a code: the warps resident at one time
+    // mostly work on one representation, whose tables then stay in L1
+    const unsigned long long nchunks = ((unsigned long long)mc.io.batch + mc.chunk - 1) / mc.chunk;
+    const int b = (int)(l / nchunks);
+    const int sblock = (int)(l - (unsigned long long)b * nchunks);
     it.c = c;
-    it.b = (int)(l - (unsigned long long)sblock * R);
+    it.b = b;
     it.s0 = sblock * mc.chunk;
     it.s1 = min(mc.io.batch, it.s0 + mc.chunk);
     return true;

@@ -1403,12 +1403,17 @@ size_t mbbp_wms_workspace_size(const mbbp_bases* B, int batch, int T, int ckpt) 
     if (!B || batch < 0 || T < 1 || ckpt < 1) return 0;
     const size_t nckpt = (size_t)((T - 1) / ckpt);
     const size_t S = (size_t)B->dev.DC * B->MP;
-    return 256 + align256((size_t)batch * B->R * nckpt * S * 4) +
-           align256((size_t)kWmsMaxWarps * ckpt * S * 4);
+    // per-warp segment buffers only when the backward pass cannot keep the
+    // segment states in shared memory
+    const size_t seg = wms_states_in_smem(B->dev, ckpt) ? 0 : align256((size_t)kWmsMaxWarps * ckpt * S * 4);
+    return 256 + align256((size_t)batch * B->R * nckpt * S * 4) + seg;
 }
 
 namespace {
+// The per-warp segment buffers (null when the backward pass keeps the
+// segment states in shared memory and the workspace has no such region).
 float* wms_seg_buf(const mbbp_bases* B, int batch, int T, int ckpt, void* workspace) {
+    if (wms_states_in_smem(B->dev, ckpt)) return nullptr;
     const size_t nckpt = (size_t)((T - 1) / ckpt);
     const size_t S = (size_t)B->dev.DC * B->MP;
     return reinterpret_cast<float*>(static_cast<char*>(workspace) + 256 +

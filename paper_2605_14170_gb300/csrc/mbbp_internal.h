@@ -214,6 +214,9 @@ struct WmsArgs {
     unsigned long long total_items;
 };
 constexpr int kWmsMaxWarps = 152 * 16;  // warps of the backward grid (segment buffers)
+// Whether the WMS backward pass keeps its segment states in shared memory
+// (then it needs no per-warp segment buffers in the workspace).
+bool wms_states_in_smem(const DevBases& B, int ckpt);
 cudaError_t launch_wms(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count);
 cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, size_t count, float lr, float b1,
                         float b2, float eps, int step, float lo, float hi, cudaStream_t s);

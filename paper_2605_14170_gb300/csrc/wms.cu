@@ -50,20 +50,23 @@ __host__ __device__ inline WmsLayout wms_layout(int DC, int MP, int n, int ckpt)
 
 // q^(t)_e and the posterior from m (variable pass, ascending row order).
 // Each step's descriptor is loaded one step ahead; a variable's slots and
-// messages are read once into registers (at most DV of them).
-template <int DV>
+// messages are read once into registers (at most DV of them).  G warps
+// share the item: the thread with group index gt takes positions gt,
+// gt + 32 G, ...
+template <int DV, int G = 1>
 __device__ __forceinline__ void wms_var_pass(const DevBases& B, int b, const uint2* vd, const float* m,
                                              float* q, const float* mu, float* post) {
-    const int lane = threadIdx.x & 31;
+    constexpr int GT = 32 * G;
+    const int lane = (int)(threadIdx.x % GT);
     const int n = B.n;
     if constexpr (DV == 6) {
         // width 6: the slots come packed in the descriptor (vdesc6), no
         // slot-list load; byte offsets index m and q alike (same layout)
         const uint4* vd6 = B.vdesc6 + (size_t)b * n;
         uint4 dn = (lane < n) ? __ldg(vd6 + lane) : make_uint4(0u, 0u, 0u, 0u);
-        for (int p = lane; p < n; p += 32) {
+        for (int p = lane; p < n; p += GT) {
             const uint4 d = dn;
-            if (p + 32 < n) dn = __ldg(vd6 + p + 32);
+            if (p + GT < n) dn = __ldg(vd6 + p + GT);
             const int v = d.x & 0xffff, deg = (int)(d.x >> 16);
             uint32_t s[6];
             float mv[6];
@@ -72,18 +75,20 @@ __device__ __forceinline__ void wms_var_pass(const DevBases& B, int b, const uin
                 s[i] = (i < deg) ? generic_bp::packed_off(d, i) : 0u;
                 mv[i] = (i < deg) ? generic_bp::msg_at(const_cast<float*>(m), s[i]) : 0.0f;
             }
-            float acc = mu[v];
+            // P[i] = mu + m_0 + ... + m_{i-1}; q_i = P[i] + m_{i+1} + ... (the
+            // ascending sum without m_i, term for term)
+            float P[7];
+            P[0] = mu[v];
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
-                if (i < deg) acc = __fadd_rn(acc, mv[i]);
-            if (post) post[v] = acc;
+            for (int i = 0; i < 6; ++i) P[i + 1] = (i < deg) ? __fadd_rn(P[i], mv[i]) : P[i];
+            if (post) post[v] = P[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 if (i < deg) {
-                    float x = mu[v];
+                    float x = P[i];
 #pragma unroll
-                    for (int k = 0; k < 6; ++k)
-                        if (k < deg && k != i) x = __fadd_rn(x, mv[k]);
+                    for (int k = i + 1; k < 6; ++k)
+                        if (k < deg) x = __fadd_rn(x, mv[k]);
                     generic_bp::msg_at(q, s[i]) = x;
                 }
             }
@@ -91,9 +96,9 @@ __device__ __forceinline__ void wms_var_pass(const DevBases& B, int b, const uin
         return;
     }
     uint2 dn = (lane < n) ? __ldg(vd + lane) : make_uint2(0u, 0u);
-    for (int p = lane; p < n; p += 32) {
+    for (int p = lane; p < n; p += GT) {
         const uint2 d = dn;
-        if (p + 32 < n) dn = __ldg(vd + p + 32);
+        if (p + GT < n) dn = __ldg(vd + p + GT);
         const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
         const uint16_t* sl = B.vslot + d.x;
         int s[DV];
@@ -103,18 +108,18 @@ __device__ __forceinline__ void wms_var_pass(const DevBases& B, int b, const uin
             s[i] = (i < deg) ? (int)__ldg(sl + i) : 0;
             mv[i] = (i < deg) ? m[s[i]] : 0.0f;
         }
-        float acc = mu[v];
+        float P[DV + 1];  // prefix sums, as in the packed branch
+        P[0] = mu[v];
 #pragma unroll
-        for (int i = 0; i < DV; ++i)
-            if (i < deg) acc = __fadd_rn(acc, mv[i]);
-        if (post) post[v] = acc;
+        for (int i = 0; i < DV; ++i) P[i + 1] = (i < deg) ? __fadd_rn(P[i], mv[i]) : P[i];
+        if (post) post[v] = P[DV];
 #pragma unroll
         for (int i = 0; i < DV; ++i) {
             if (i < deg) {
-                float x = mu[v];
+                float x = P[i];
 #pragma unroll
-                for (int k = 0; k < DV; ++k)
-                    if (k < deg && k != i) x = __fadd_rn(x, mv[k]);
+                for (int k = i + 1; k < DV; ++k)
+                    if (k < deg) x = __fadd_rn(x, mv[k]);
                 q[s[i]] = x;
             }
         }
@@ -122,16 +127,19 @@ __device__ __forceinline__ void wms_var_pass(const DevBases& B, int b, const uin
 }
 
 // One WMS check pass: m <- g m + (1 - g) w S mn(q).  wt, gt: parameters of
-// this iteration for representation b ([E] in row-major edge order).
-template <int DC>
+// this iteration for representation b ([E] in row-major edge order).  With G
+// warps per item the thread with group index gt takes rows gt, gt + 32 G,
+// ...; bit k of sb is the syndrome bit of its k-th row.
+template <int DC, int G = 1>
 __device__ __forceinline__ void wms_check_pass(const DevBases& B, int b, const uint32_t* rinfo,
                                                int Mb, uint32_t sb, const float* q, float* m,
                                                const float* wt, const float* gt) {
-    const int lane = threadIdx.x & 31;
+    constexpr int GT = 32 * G;
+    const int lane = (int)(threadIdx.x % GT);
     const int MP = B.MP;
     const int32_t* rp = B.rowptr + (size_t)b * MP;
-    for (int k = 0; k < (MP >> 5); ++k) {
-        const int r = lane + 32 * k;
+    for (int k = 0; k < (MP + GT - 1) / GT; ++k) {
+        const int r = lane + GT * k;
         if (r >= Mb) continue;
         const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
         const int e0 = __ldg(rp + r);
@@ -171,23 +179,33 @@ __device__ __forceinline__ float bce_neg_sigmoid(float post, int e) {
     return x > 0.f ? x + log1pf(expf(-x)) : log1pf(expf(x));
 }
 
-template <int DC, int DV>
+// G warps decode each item together (G = 1: one warp per item; G > 1 for
+// codes whose two message arrays per item, not registers, limit the resident
+// warps).  Group g of the block uses named barrier 1 + g; the arithmetic of
+// every row and variable is the same whatever G.
+template <int DC, int DV, int G = 1>
 __global__ void __launch_bounds__(kWmsWarps * 32)
 wms_forward_kernel(const WmsArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long group_item[kWmsWarps];
+    __shared__ float group_part[kWmsWarps];
+    constexpr int GT = 32 * G;
     const DevBases& B = a.B;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    const int lane = (int)(threadIdx.x % GT);  // the thread's index in its group
+    const int wig = lane >> 5;                  // the warp's index in its group
+    const int grp = (int)(threadIdx.x >> 5) / G;
+    const int bar = 1 + grp;
     const int MP = B.MP, n = B.n, m_rows = B.m, R = B.R, W = B.W;
     const WmsLayout L = wms_layout(DC, MP, n, a.ckpt);
-    float* m = reinterpret_cast<float*>(smem + warp * L.fwd_bytes);
+    float* m = reinterpret_cast<float*>(smem + grp * L.fwd_bytes);
     float* q = m + L.S;
     float* mu = q + L.S;
     float* post = mu + L.npad;
     uint8_t* eh = reinterpret_cast<uint8_t*>(post + L.npad);
-    const int orow_steps = B.mpad >> 5;
+    const int orow_steps = (B.mpad + GT - 1) / GT;
+    const int row_steps = (MP + GT - 1) / GT;
     // H's columns for the halting test, once per block
-    uint16_t* hcol_s = reinterpret_cast<uint16_t*>(smem + (blockDim.x >> 5) * L.fwd_bytes);
+    uint16_t* hcol_s = reinterpret_cast<uint16_t*>(smem + (blockDim.x / GT) * L.fwd_bytes);
     if (a.decode) {
         for (int i = threadIdx.x; i < DC * B.mpad; i += blockDim.x) hcol_s[i] = __ldg(B.hcol + i);
         __syncthreads();
@@ -198,8 +216,15 @@ wms_forward_kernel(const WmsArgs a) {
     const unsigned long long batch = a.total_items / (unsigned long long)R;
     for (;;) {
         unsigned long long g = 0;
-        if (lane == 0) g = atomicAdd(a.counter, 1ull);
-        g = __shfl_sync(kFull, g, 0);
+        if constexpr (G == 1) {
+            if (lane == 0) g = atomicAdd(a.counter, 1ull);
+            g = __shfl_sync(kFull, g, 0);
+        } else {
+            // rewritten only after the item's last barrier, which every reader passed
+            if (lane == 0) group_item[grp] = atomicAdd(a.counter, 1ull);
+            generic_bp::gsync<G>(bar);
+            g = group_item[grp];
+        }
         if (g >= a.total_items) break;
         const int b = (int)(g / batch);
         const int shot = (int)(g - (unsigned long long)b * batch);
@@ -209,26 +234,26 @@ wms_forward_kernel(const WmsArgs a) {
         const int Mb = __ldg(B.rows + b);
         const float* llr = a.llr + (size_t)shot * a.llr_stride;
         const uint8_t* sy = a.synd + (size_t)shot * m_rows;
-        for (int v = lane; v < n; v += 32) {
+        for (int v = lane; v < n; v += GT) {
             const float x = __fadd_rn(__ldg(llr + v), 0.0f);  // -0 -> +0 (sign bits decide the check rule)
             mu[v] = x;
             post[v] = x;
             eh[v] = (x < 0.f) ? 1 : 0;
         }
         if (lane == 0) eh[n] = 0;
-        for (int i = lane; i < L.S; i += 32) m[i] = 0.0f;
+        for (int i = lane; i < L.S; i += GT) m[i] = 0.0f;
         uint32_t sb = 0;
-        for (int k = 0; k < (MP >> 5); ++k) {
-            const int r = lane + 32 * k;
+        for (int k = 0; k < row_steps; ++k) {
+            const int r = lane + GT * k;
             if (r < Mb) sb |= (uint32_t)(__ldg(sy + (__ldg(rinfo + r) & 0xffffu)) & 1u) << k;
         }
-        __syncwarp();
-        for (int p = lane; p < n; p += 32) {  // q^(0) = mu
+        generic_bp::gsync<G>(bar);
+        for (int p = lane; p < n; p += GT) {  // q^(0) = mu
             const uint2 d = __ldg(vd + p);
             const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
             for (int i = 0; i < deg; ++i) q[__ldg(B.vslot + d.x + i)] = mu[v];
         }
-        __syncwarp();
+        generic_bp::gsync<G>(bar);
         int K = 0;
         bool conv = false;
         float lacc = 0.f;  // this lane's BCE of the posteriors of iterations 1..T-1 (all_iters)
@@ -237,7 +262,7 @@ wms_forward_kernel(const WmsArgs a) {
             if (a.decode) {
                 bool ok = true;
                 for (int k = 0; k < orow_steps; ++k) {
-                    const int r = lane + 32 * k;
+                    const int r = lane + GT * k;
                     if (r < m_rows) {
                         uint32_t par = (sb >> k) & 1u;
 #pragma unroll
@@ -245,7 +270,7 @@ wms_forward_kernel(const WmsArgs a) {
                         ok = ok && (par == 0u);
                     }
                 }
-                if (__all_sync(kFull, ok)) {
+                if (generic_bp::gall<G>(ok, bar)) {
                     conv = true;
                     K = it;
                     break;
@@ -258,36 +283,33 @@ wms_forward_kernel(const WmsArgs a) {
             const int tp = min(it, a.T - 1);  // iterations past T reuse the last weights
             const float* wt = a.w + ((size_t)b * a.T + tp) * a.E;
             const float* gt = a.g + ((size_t)b * a.T + tp) * a.E;
-            wms_check_pass<DC>(B, b, rinfo, Mb, sb, q, m, wt, gt);
-            __syncwarp();
-            wms_var_pass<DV>(B, b, vd, m, q, mu, post);
-            __syncwarp();
+            wms_check_pass<DC, G>(B, b, rinfo, Mb, sb, q, m, wt, gt);
+            generic_bp::gsync<G>(bar);
+            wms_var_pass<DV, G>(B, b, vd, m, q, mu, post);
+            generic_bp::gsync<G>(bar);
             if (a.decode) {
-                for (int v = lane; v < n; v += 32) eh[v] = (post[v] < 0.f) ? 1 : 0;
-                __syncwarp();
+                for (int v = lane; v < n; v += GT) eh[v] = (post[v] < 0.f) ? 1 : 0;
+                generic_bp::gsync<G>(bar);
             } else {
                 if (a.ckpt_buf && (it + 1) % a.ckpt == 0 && it + 1 < a.T) {
                     float* dst = a.ckpt_buf + ((size_t)item * a.nckpt + ((it + 1) / a.ckpt - 1)) * L.S;
-                    for (int i = lane; i < L.S; i += 32) dst[i] = m[i];
+                    for (int i = lane; i < L.S; i += GT) dst[i] = m[i];
                 }
                 if (a.all_iters && a.etrue && a.loss && it + 1 < a.T) {
-                    for (int v = lane; v < n; v += 32)
+                    for (int v = lane; v < n; v += GT)
                         lacc += bce_neg_sigmoid(post[v], (int)((__ldg(a.etrue + (size_t)shot * W + (v >> 5)) >> (v & 31)) & 1u));
                 }
             }
         }
         if (a.post)
-            for (int v = lane; v < n; v += 32) a.post[item * n + v] = post[v];
+            for (int v = lane; v < n; v += GT) a.post[item * n + v] = post[v];
         if (a.decode) {
-            uint32_t myword = 0;
-            for (int w = 0; w < W; ++w) {
-                const int v = 32 * w + lane;
+            // warp wig packs the candidate words wig, wig + G, ...
+            const int wl = lane & 31;
+            for (int w = wig; w < W; w += G) {
+                const int v = 32 * w + wl;
                 const uint32_t word = __ballot_sync(kFull, v < n && eh[v]);
-                if ((w & 31) == lane) myword = word;
-                if ((w & 31) == 31 || w == W - 1) {
-                    const int base = w & ~31;
-                    if (base + lane <= w) a.cand[item * W + base + lane] = myword;
-                }
+                if (wl == 0) a.cand[item * W + w] = word;
             }
             if (lane == 0) {
                 a.conv[item] = conv ? 1 : 0;
@@ -295,14 +317,21 @@ wms_forward_kernel(const WmsArgs a) {
             }
         } else if (a.etrue && a.loss) {
             float acc = 0.f;
-            for (int v = lane; v < n; v += 32)
+            for (int v = lane; v < n; v += GT)
                 acc += bce_neg_sigmoid(post[v], (int)((__ldg(a.etrue + (size_t)shot * W + (v >> 5)) >> (v & 31)) & 1u));
             acc += lacc;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+            if constexpr (G > 1) {
+                // the group's warps' sums, added in warp order
+                if ((lane & 31) == 0) group_part[grp * G + wig] = acc;
+                generic_bp::gsync<G>(bar);
+                if (lane == 0)
+                    for (int w = 1; w < G; ++w) acc += group_part[grp * G + w];
+            }
             if (lane == 0) a.loss[item] = a.scale * acc * (a.all_iters ? 1.0f / a.T : 1.0f);
         }
-        __syncwarp();
+        generic_bp::gsync<G>(bar);
     }
 }
 
@@ -506,26 +535,68 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ gra
     p[i] = fminf(fmaxf(x, lo), hi);
 }
 
+template <int K, int G>
+cudaError_t launch_forward_g(const WmsArgs& a, size_t fixed, size_t per_item, int warps, int per_sm,
+                             cudaStream_t s, int sm_count) {
+    const unsigned long long groups = (unsigned long long)(warps / G);
+    const size_t smem = fixed + groups * per_item;
+    unsigned long long want = (a.total_items + groups - 1) / groups;
+    unsigned long long grid = (unsigned long long)per_sm * sm_count;
+    if (want < grid) grid = want;
+    wms_forward_kernel<K, K, G><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count) {
     const WmsLayout L = wms_layout(K, a.B.MP, a.B.n, a.ckpt);
-    // backward: keep the segment states in shared memory when four warps'
-    // worth fits in about half of an SM's shared memory
+    if (!backward) {
+        // forward / decode: G warps per item, G in {1, 2, 4}; per G the block
+        // size (a multiple of G, up to 8 warps) with the most resident warps
+        // per SM within 200 KB of shared memory per block (H's columns once,
+        // then one area per item); a larger G only when it holds at least
+        // half again as many warps as the best smaller one
+        if (L.fwd_bytes > 200 * 1024) return cudaErrorInvalidConfiguration;
+        const size_t fixed = (size_t)((K * a.B.mpad * 2 + 15) & ~15);
+        const void* kerns[3] = {reinterpret_cast<const void*>(wms_forward_kernel<K, K, 1>),
+                                reinterpret_cast<const void*>(wms_forward_kernel<K, K, 2>),
+                                reinterpret_cast<const void*>(wms_forward_kernel<K, K, 4>)};
+        int best_g = -1, best_w = 0, best_b = 0;
+        for (int gi = 0; gi < 3; ++gi) {
+            const int G = 1 << gi;
+            int warps = 0, per_sm = 0;
+            for (int w = G; w <= kWmsWarps && fixed + (size_t)(w / G) * L.fwd_bytes <= 200 * 1024; w += G) {
+                int b = 0;
+                cudaError_t e = prepare_kernel(kerns[gi], w * 32, fixed + (size_t)(w / G) * L.fwd_bytes, &b);
+                if (e != cudaSuccess) return e;
+                if (b * w > per_sm * warps) {
+                    warps = w;
+                    per_sm = b;
+                }
+            }
+            if (warps > 0 && (best_g < 0 || 2 * warps * per_sm >= 3 * best_w * best_b)) {
+                best_g = gi;
+                best_w = warps;
+                best_b = per_sm;
+            }
+        }
+        if (best_g < 0) return cudaErrorInvalidConfiguration;
+        if (best_g == 0) return launch_forward_g<K, 1>(a, fixed, L.fwd_bytes, best_w, best_b, s, sm_count);
+        if (best_g == 1) return launch_forward_g<K, 2>(a, fixed, L.fwd_bytes, best_w, best_b, s, sm_count);
+        return launch_forward_g<K, 4>(a, fixed, L.fwd_bytes, best_w, best_b, s, sm_count);
+    }
     const size_t st_bytes = (size_t)a.ckpt * L.S * 4;
-    const bool smem_st = backward && (size_t)kWmsStateWarps * (L.bwd_bytes + st_bytes) <= 110 * 1024;
-    const size_t per_warp = backward ? L.bwd_bytes + (smem_st ? st_bytes : 0) : L.fwd_bytes;
+    const bool smem_st = wms_states_in_smem(a.B, a.ckpt);
+    const size_t per_warp = L.bwd_bytes + (smem_st ? st_bytes : 0);
     if (per_warp > 200 * 1024) return cudaErrorInvalidConfiguration;
-    // the forward kernel also holds H's columns once per block (halting test)
-    const size_t fixed = backward ? 0 : (size_t)((K * a.B.mpad * 2 + 15) & ~15);
-    const void* kern = !backward ? reinterpret_cast<const void*>(wms_forward_kernel<K, K>)
-                       : smem_st ? reinterpret_cast<const void*>(wms_backward_kernel<K, K, true>)
-                                 : reinterpret_cast<const void*>(wms_backward_kernel<K, K, false>);
+    const void* kern = smem_st ? reinterpret_cast<const void*>(wms_backward_kernel<K, K, true>)
+                               : reinterpret_cast<const void*>(wms_backward_kernel<K, K, false>);
     // the block size with the most resident warps per SM (ties: the smaller
     // block), within 200 KB of shared memory per block
     int warps = 0, per_sm = 0;
-    for (int w = 1; w <= kWmsWarps && fixed + (size_t)w * per_warp <= 200 * 1024; ++w) {
+    for (int w = 1; w <= kWmsWarps && (size_t)w * per_warp <= 200 * 1024; ++w) {
         int b = 0;
-        cudaError_t e = prepare_kernel(kern, w * 32, fixed + (size_t)w * per_warp, &b);
+        cudaError_t e = prepare_kernel(kern, w * 32, (size_t)w * per_warp, &b);
         if (e != cudaSuccess) return e;
         if (b * w > per_sm * warps) {
             warps = w;
@@ -533,24 +604,28 @@ cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm
         }
     }
     if (warps == 0) return cudaErrorInvalidConfiguration;
-    const size_t smem = fixed + warps * per_warp;
+    const size_t smem = warps * per_warp;
     unsigned long long want = (a.total_items + warps - 1) / warps;
     unsigned long long grid = (unsigned long long)per_sm * sm_count;
     if (want < grid) grid = want;
-    if (backward) {  // one segment buffer per warp: at most kWmsMaxWarps warps
-        const unsigned long long cap = kWmsMaxWarps / warps;
-        if (grid > cap) grid = cap;
-    }
-    if (backward && smem_st)
+    // one segment buffer per warp: at most kWmsMaxWarps warps
+    const unsigned long long cap = kWmsMaxWarps / warps;
+    if (grid > cap) grid = cap;
+    if (smem_st)
         wms_backward_kernel<K, K, true><<<(unsigned)grid, warps * 32, smem, s>>>(a);
-    else if (backward)
-        wms_backward_kernel<K, K, false><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     else
-        wms_forward_kernel<K, K><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+        wms_backward_kernel<K, K, false><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+bool wms_states_in_smem(const DevBases& B, int ckpt) {
+    // the backward pass keeps a segment's states in shared memory when four
+    // warps' worth fits in about half of an SM's shared memory
+    const WmsLayout L = wms_layout(B.DC, B.MP, B.n, ckpt);
+    return (size_t)kWmsStateWarps * (L.bwd_bytes + (size_t)ckpt * L.S * 4) <= 110 * 1024;
+}
 
 cudaError_t launch_wms(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count) {
     if (a.B.DC == 6) return launch_wms_t<6>(a, backward, s, sm_count);
