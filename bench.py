@@ -51,10 +51,11 @@ OPS_PER_EDGE_UPDATE = 10  # algorithmic ALU operations per edge-update (min-sum 
 ALU_OPS, FMA_OPS = 7, 3
 ALU_LANES, FMA_LANES, ISSUE_LANES = 64, 128, 128
 EDGE_UPDATES_PER_CLK_SM = min(ALU_LANES / ALU_OPS, FMA_LANES / FMA_OPS, ISSUE_LANES / OPS_PER_EDGE_UPDATE)
-# DRAM bytes per shot of the BP kernel from one ncu capture of a 100k-shot
-# launch of the current build; None until that capture is taken, and again
-# once the kernel changes
-DRAM_BYTES_PER_SHOT = None
+# DRAM bytes per shot of the BP kernel: one ncu capture of a 100k-shot launch
+# of the current kernel (profiles/decode_small_kernel_bb144_r16.md: 7.312 MB
+# read + 2.0 KB written); set to None whenever the kernel changes until it is
+# captured again
+DRAM_BYTES_PER_SHOT = (7.311616e6 + 2.048e3) / 100000
 WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
 
 
@@ -936,8 +937,8 @@ def main():
                          "unit": "Tops/s", "frac": achieved_ops / peak_ops_128,
                          "traffic": DRAM_BYTES_PER_SHOT * S if DRAM_BYTES_PER_SHOT is not None else None,
                          "traffic_note": "dram read+write of the BP kernel from one ncu capture of a "
-                                         "100k-shot launch (profiles/decode_small_kernel_bb144_r16.md), "
-                                         "scaled by shots",
+                                         "100k-shot launch of the current kernel "
+                                         "(profiles/decode_small_kernel_bb144_r16.md), scaled by shots",
                          "kernel": "mbbp_decode (BP + FWS)", "decode_ms_avg": dec_avg_ms,
                          "edge_updates_per_launch": edge_per_launch,
                          "ops_per_edge_update": OPS_PER_EDGE_UPDATE,
