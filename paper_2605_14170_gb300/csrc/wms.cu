@@ -338,7 +338,7 @@ wms_forward_kernel(const WmsArgs a) {
 // SMEM_ST: the segment's recomputed states sit in shared memory after the
 // warp's other arrays (small codes); otherwise in the warp's global buffer.
 template <int DC, int DV, bool SMEM_ST>
-__global__ void __launch_bounds__(kWmsWarps * 32)
+__global__ void __launch_bounds__(kWmsWarps * 32, 4)
 wms_backward_kernel(const WmsArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevBases& B = a.B;
@@ -443,6 +443,14 @@ wms_backward_kernel(const WmsArgs a) {
                     if (r >= Mb) continue;
                     const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
                     const int e0 = __ldg(rp + r);
+                    // the row's parameters first: L2 loads (the shared memory
+                    // leaves little L1) that then overlap the arithmetic below
+                    float wv[DC], gv[DC];
+#pragma unroll
+                    for (int j = 0; j < DC; ++j) {
+                        wv[j] = (j < deg) ? __ldg(wt + e0 + j) : 0.0f;
+                        gv[j] = (j < deg) ? __ldg(gt + e0 + j) : 0.0f;
+                    }
                     float qq[DC];
 #pragma unroll
                     for (int j = 0; j < DC; ++j) qq[j] = (j < deg) ? q[j * MP + r] : MBBP_LMAX;
@@ -473,7 +481,7 @@ wms_backward_kernel(const WmsArgs a) {
                         const float mn = own ? min2 : min1;
                         const uint32_t neg = par ^ ((qq[j] < 0.f) ? 1u : 0u);
                         const float sgn = neg ? -1.0f : 1.0f;
-                        const float ww = __ldg(wt + e0 + j), gg = __ldg(gt + e0 + j);
+                        const float ww = wv[j], gg = gv[j];
                         const float gmj = gm[j * MP + r];
                         const float c = ww * sgn * mn;
                         atomicAdd(ggt + e0 + j, gmj * (mprev[j * MP + r] - c));
@@ -494,7 +502,36 @@ wms_backward_kernel(const WmsArgs a) {
                     }
                 }
                 __syncwarp();
-                if (t >= 2) {
+                if (t >= 2 && DV == 6) {
+                    // width 6: the same pass with the slots from the packed
+                    // descriptors, each step's descriptor loaded one step ahead
+                    const uint4* vd6 = B.vdesc6 + (size_t)b * n;
+                    uint4 dn = (lane < n) ? __ldg(vd6 + lane) : make_uint4(0u, 0u, 0u, 0u);
+                    for (int p = lane; p < n; p += 32) {
+                        const uint4 d = dn;
+                        if (p + 32 < n) dn = __ldg(vd6 + p + 32);
+                        const int v = d.x & 0xffff, deg = (int)(d.x >> 16);
+                        uint32_t o[6];
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) o[i] = generic_bp::packed_off(d, i);
+                        float G = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < 6; ++i)
+                            if (i < deg) G += generic_bp::msg_at(gq, o[i]);
+                        float gp = 0.0f;
+                        if (a.all_iters) {
+                            float acc = mu[v];
+#pragma unroll
+                            for (int i = 0; i < 6; ++i)
+                                if (i < deg) acc = __fadd_rn(acc, generic_bp::msg_at(const_cast<float*>(mprev), o[i]));
+                            const uint32_t ev = (__ldg(a.etrue + (size_t)shot * B.W + (v >> 5)) >> (v & 31)) & 1u;
+                            gp = lw * ((float)ev - 1.0f / (1.0f + expf(acc)));
+                        }
+#pragma unroll
+                        for (int i = 0; i < 6; ++i)
+                            if (i < deg) generic_bp::msg_at(gm, o[i]) += G - generic_bp::msg_at(gq, o[i]) + gp;
+                    }
+                } else if (t >= 2) {
                     for (int p = lane; p < n; p += 32) {
                         const uint2 d = __ldg(vd + p);
                         const int v = d.y & 0xffff, deg = (int)(d.y >> 16);
