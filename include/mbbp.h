@@ -38,7 +38,9 @@ typedef enum {
     MBBP_E_INVALID = 1,   /* an argument is out of range or inconsistent      */
     MBBP_E_TOO_LARGE = 2, /* sizes beyond the limits below                    */
     MBBP_E_CUDA = 3,      /* a CUDA runtime call failed                       */
-    MBBP_E_TIMEOUT = 4,   /* a bounded device-side wait gave up               */
+    MBBP_E_TIMEOUT = 4,   /* reserved for a bounded device-side wait; no entry
+                             point of this build waits on the device (work is
+                             pulled with atomic counters), so none returns it */
     MBBP_E_NOMEM = 5,     /* host or device allocation failed                 */
     MBBP_E_NOT_FOUND = 6  /* fewer distinct subtrees than requested exist     */
 } mbbp_status;
