@@ -111,14 +111,15 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
 // (|q| <= |mu| + 6 LMAX).
 //
 // The update runs for the 32 lanes of a variable step at once: DM is the largest
-// degree among the step's lanes (warp-uniform).  A lane of degree deg < DM
-// loads nothing for its edges i >= deg and takes them as +0.0, which leaves
-// every sum unchanged (x + 0 = x exactly for every x but -0, and no sum here
-// is -0: they start from mu + 0 and a sum that cancels rounds to +0); it
-// stores only its own deg messages.  Each lane's sums are therefore those of
-// its own degree (same terms, same order, exact), while the step issues one
-// load and one store instruction per edge position instead of one per
-// degree case present among its lanes.
+// degree among the step's lanes (warp-uniform).  The descriptor of a lane of
+// degree deg < DM points its edges i >= deg at the warp's zero slot, so the
+// lane loads +0.0 for them, which leaves every sum unchanged (x + 0 = x
+// exactly for every x but -0, and no sum here is -0: they start from mu + 0
+// and a sum that cancels rounds to +0); it stores only its own deg messages,
+// so the zero slot stays zero.  Each lane's sums are therefore those of its
+// own degree (same terms, same order, exact), while the step issues one load
+// and one store instruction per edge position instead of one per degree
+// case present among its lanes.
 template <int DM>
 __device__ __forceinline__ float var_upd_step(char* smc, const uint4& d, float mu, int deg) {
     uint32_t a[DM];
@@ -126,7 +127,7 @@ __device__ __forceinline__ float var_upd_step(char* smc, const uint4& d, float m
 #pragma unroll
     for (int i = 0; i < DM; ++i) a[i] = addr_of(d, i);
 #pragma unroll
-    for (int i = 0; i < DM; ++i) m[i] = (i < deg) ? lds(smc, a[i]) : 0.0f;
+    for (int i = 0; i < DM; ++i) m[i] = lds(smc, a[i]);
     float P[DM + 1];
     P[0] = mu;
 #pragma unroll

@@ -29,10 +29,10 @@ void* g_scratch_addr[kMaxDevices] = {};
 // several small ones.  Each class is compiled for its own block size.
 constexpr int kGenericWideWarps = 16;
 
-// G warps decode each item together (G = 1: one warp per item; G = 2 for
-// codes whose per-item shared memory, not registers, limits the resident
-// warps: the same shared memory then holds twice the warps).  Group g of the
-// block uses named barrier 1 + g.
+// G warps decode each item together (G = 1: one warp per item; G = 2 or 4
+// for codes whose per-item shared memory, not registers, limits the resident
+// warps: the same shared memory then holds G times the warps).  Group g of
+// the block uses named barrier 1 + g (at most 8 groups: ids 1..8).
 template <int DC, int DV, int RULE, int MAXW, bool TRACE = false, int G = 1>
 __global__ void __launch_bounds__(MAXW * 32)
 decode_kernel(const DecodeArgs a) {
@@ -234,26 +234,44 @@ cudaError_t launch_serial_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
     return cudaGetLastError();
 }
 
+template <int K, int RULE, bool TRACE, int G>
+cudaError_t launch_decode_g(const DecodeArgs& a, int cls, int warps, int per_sm, size_t smem, cudaStream_t s,
+                            int sm_count) {
+    const unsigned long long groups = (unsigned long long)(warps / G);
+    unsigned long long want = (a.total_items + groups - 1) / groups;
+    unsigned long long grid = (unsigned long long)per_sm * (unsigned long long)sm_count;
+    if (want < grid) grid = want;
+    const dim3 gd((unsigned)grid), bd((unsigned)(warps * 32));
+    if (cls == 0)
+        decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, G><<<gd, bd, smem, s>>>(a);
+    else
+        decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, G><<<gd, bd, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int K, int RULE, bool TRACE>
 cudaError_t launch_decode_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
-    // Launch shapes: (block class, warps per item G).  The narrow class runs
-    // blocks of up to 8 warps, the wide class up to 16 (compiled for
-    // 512-thread blocks, it takes more registers).  For each shape, the
+    // Launch shapes: (block class, warps per item G in {1, 2, 4}).  The narrow
+    // class runs blocks of up to 8 warps, the wide class up to 16 (compiled
+    // for 512-thread blocks, it takes more registers).  For each shape, the
     // block size with the most resident warps per SM (ties: the smaller
     // block) within 200 KB of shared memory per block; a block holds H's
-    // columns once plus one message area per item.  G = 2 is taken when it
-    // holds at least half again as many warps as G = 1 (codes whose message
-    // areas, not registers, limit the resident warps); among G = 1 shapes
-    // the wide class only when it holds at least a quarter more warps.
-    const void* kerns[2][2] = {
+    // columns once plus one message area per item.  Among G = 1 shapes the
+    // wide class only when it holds at least a quarter more warps; a larger G
+    // only when it holds at least half again as many warps as the best
+    // smaller one (codes whose message areas, not registers, limit the
+    // resident warps).
+    const void* kerns[3][2] = {
         {reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 1>),
          reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 1>)},
         {reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 2>),
-         reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 2>)}};
+         reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 2>)},
+        {reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 4>),
+         reinterpret_cast<const void*>(decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 4>)}};
     const generic_bp::WarpLayout L = generic_bp::warp_layout(K, a.B.MP, a.B.mpad, a.B.n);
-    int choice[2][2][2] = {};  // [G-1][class] = {warps per block, blocks per SM}
-    for (int gi = 0; gi < 2; ++gi) {
-        const int G = gi + 1;
+    int choice[3][2][2] = {};  // [log2 G][class] = {warps per block, blocks per SM}
+    for (int gi = 0; gi < 3; ++gi) {
+        const int G = 1 << gi;
         for (int w = G; w <= kGenericWideWarps; w += G) {
             const size_t sm_w = (size_t)L.hcol_bytes + (size_t)(w / G) * L.per_warp;
             if (sm_w > 200 * 1024) break;
@@ -268,24 +286,20 @@ cudaError_t launch_decode_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
         }
     }
     auto resident = [&](int gi, int cls) { return choice[gi][cls][0] * choice[gi][cls][1]; };
-    const int best1 = resident(0, 1) * 4 >= resident(0, 0) * 5 ? 1 : 0;
-    const int best2 = resident(1, 1) > resident(1, 0) ? 1 : 0;
-    const bool use_g2 = 2 * resident(1, best2) >= 3 * resident(0, best1);
-    const int gi = use_g2 ? 1 : 0, cls = use_g2 ? best2 : best1;
-    const int warps = choice[gi][cls][0], per_sm = choice[gi][cls][1];
+    int gi_best = 0, cls_best = resident(0, 1) * 4 >= resident(0, 0) * 5 ? 1 : 0;
+    for (int gi = 1; gi < 3; ++gi) {
+        const int cls = resident(gi, 1) > resident(gi, 0) ? 1 : 0;
+        if (2 * resident(gi, cls) >= 3 * resident(gi_best, cls_best)) {
+            gi_best = gi;
+            cls_best = cls;
+        }
+    }
+    const int warps = choice[gi_best][cls_best][0], per_sm = choice[gi_best][cls_best][1];
     if (warps == 0) return cudaErrorInvalidConfiguration;
-    const int G = gi + 1;
-    const size_t smem = (size_t)L.hcol_bytes + (size_t)(warps / G) * L.per_warp;
-    const unsigned long long groups = (unsigned long long)(warps / G);
-    unsigned long long want = (a.total_items + groups - 1) / groups;
-    unsigned long long grid = (unsigned long long)per_sm * (unsigned long long)sm_count;
-    if (want < grid) grid = want;
-    const dim3 gd((unsigned)grid), bd((unsigned)(warps * 32));
-    if (gi == 0 && cls == 0) decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 1><<<gd, bd, smem, s>>>(a);
-    if (gi == 0 && cls == 1) decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 1><<<gd, bd, smem, s>>>(a);
-    if (gi == 1 && cls == 0) decode_kernel<K, K, RULE, kWarpsPerBlock, TRACE, 2><<<gd, bd, smem, s>>>(a);
-    if (gi == 1 && cls == 1) decode_kernel<K, K, RULE, kGenericWideWarps, TRACE, 2><<<gd, bd, smem, s>>>(a);
-    return cudaGetLastError();
+    const size_t smem = (size_t)L.hcol_bytes + (size_t)(warps >> gi_best) * L.per_warp;
+    if (gi_best == 0) return launch_decode_g<K, RULE, TRACE, 1>(a, cls_best, warps, per_sm, smem, s, sm_count);
+    if (gi_best == 1) return launch_decode_g<K, RULE, TRACE, 2>(a, cls_best, warps, per_sm, smem, s, sm_count);
+    return launch_decode_g<K, RULE, TRACE, 4>(a, cls_best, warps, per_sm, smem, s, sm_count);
 }
 
 template <int K, int RULE>
