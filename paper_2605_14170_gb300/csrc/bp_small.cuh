@@ -48,9 +48,10 @@ __device__ __forceinline__ void sts(char* smc, uint32_t off, float v) {
 
 // Check update of one row (one row per lane) whose messages q[] were loaded
 // from byte offsets cb[j] + 128 k: Eq. (2) with the syndrome sign, or the
-// sum-product rule through Gallager's phi.  TRACE also writes every message
-// to tr[edge id], the edge id of slot j * MP + ((lane + rot(j)) & 31) + 32 k
-// coming from se (the representation's slot-to-edge table).
+// sum-product rule through Gallager's phi.  With TRACE and a trace pointer
+// tr, every message also goes to tr[edge id], the edge id of slot
+// j * MP + ((lane + rot(j)) & 31) + 32 k coming from se (the
+// representation's slot-to-edge table).
 template <int K, int RULE, bool REG, bool TRACE>
 __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const uint32_t (&cb)[K],
                                           int k, int deg, bool valid, uint32_t sbit, float alpha,
@@ -77,7 +78,7 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
             const uint32_t out = mag ^ ((sx ^ __float_as_uint(q[j])) & 0x80000000u);
             if (valid && (REG || j < deg)) {
                 sts(smc, cb[j] + 128 * k, __uint_as_float(out));
-                if (TRACE) tr[__ldg(se + j * MP + ((lane + slot_rot(j)) & 31) + 32 * k)] = __uint_as_float(out);
+                if (TRACE && tr) tr[__ldg(se + j * MP + ((lane + slot_rot(j)) & 31) + 32 * k)] = __uint_as_float(out);
             }
         }
     } else {
@@ -95,7 +96,7 @@ __device__ __forceinline__ void check_row(char* smc, const float (&q)[K], const 
             const uint32_t out = (__float_as_uint(mag) ^ sx) ^ (__float_as_uint(q[j]) & 0x80000000u);
             if (valid && (REG || j < deg)) {
                 sts(smc, cb[j] + 128 * k, __uint_as_float(out));
-                if (TRACE) tr[__ldg(se + j * MP + ((lane + slot_rot(j)) & 31) + 32 * k)] = __uint_as_float(out);
+                if (TRACE && tr) tr[__ldg(se + j * MP + ((lane + slot_rot(j)) & 31) + 32 * k)] = __uint_as_float(out);
             }
             pre = __fadd_rn(pre, f[j]);
         }
@@ -156,9 +157,11 @@ __device__ __forceinline__ float var_step(char* smc, int dmax, int deg, const ui
 
 // Decode shots [shot_begin, shot_end) on representation b.  smc is the
 // dynamic shared array, wbase the byte offset of this warp's area in it.
-// TRACE: io.c2v receives the check messages of every iteration (the last
-// one run remains).
-template <int VS, int RS, int ORS, int RULE, bool REG, bool TRACE = false>
+// OUT: the call asks for per-representation outputs beyond the candidates:
+// io.post (posteriors) and / or io.c2v (the check messages of every
+// iteration; the last one run remains); without OUT neither is written and
+// the loops carry no test for them.
+template <int VS, int RS, int ORS, int RULE, bool REG, bool OUT = false>
 __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, int b, int shot_begin,
                                           int shot_end, char* smc, uint32_t wbase) {
     constexpr int K = 6;
@@ -212,7 +215,7 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
         const unsigned long long item = (unsigned long long)shot * R + b;
         const float* llr = io.llr + (size_t)shot * io.llr_stride;
         const uint8_t* sy = io.synd + (size_t)shot * m;
-        float* tr = TRACE ? io.c2v + item * (unsigned long long)io.c2v_stride : nullptr;
+        float* tr = (OUT && io.c2v) ? io.c2v + item * (unsigned long long)io.c2v_stride : nullptr;
         float mu[VS];
         uint32_t ew[VS];
 #pragma unroll
@@ -239,7 +242,7 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
             for (int i = 0; i < K; ++i)
                 if (i < deg) sts(smc, addr_of(desc[k], i), mu[k]);
         }
-        if (io.post) {
+        if (OUT && io.post) {
 #pragma unroll
             for (int k = 0; k < VS; ++k)
                 if (32 * k + lane < n) io.post[item * n + (__ldg(&vd[32 * k + lane].x) & 0xffffu)] = mu[k];
@@ -294,7 +297,7 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
                 if (32 * k < Mb) {
                     const bool valid = lane + 32 * k < Mb;
                     const int deg = REG ? K : (int)((rowdeg >> (4 * k)) & 0xfu);
-                    check_row<K, RULE, REG, TRACE>(smc, q[k], cb, k, deg, valid, (sb >> k) & 1u, io.alpha, tr,
+                    check_row<K, RULE, REG, OUT>(smc, q[k], cb, k, deg, valid, (sb >> k) & 1u, io.alpha, tr,
                                                    B.sedge + (size_t)b * K * MP, MP);
                 }
             }
@@ -306,7 +309,7 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
                     const int deg = (int)((degs >> (3 * k)) & 7u);
                     const float post = var_step(smc, (int)((degs >> (16 + 3 * k)) & 7u), deg, desc[k], mu[k]);
                     ew[k] = __ballot_sync(kFull, post < 0.f);
-                    if (io.post && 32 * k + lane < n)
+                    if (OUT && io.post && 32 * k + lane < n)
                         io.post[item * n + (__ldg(&vd[32 * k + lane].x) & 0xffffu)] = post;
                 }
             }

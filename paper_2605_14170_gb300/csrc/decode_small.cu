@@ -10,7 +10,7 @@ namespace {
 constexpr int kSmallWarps = 1;  // warps per block: each warp works alone
 constexpr int kChunk = 8;       // shots per work item of a warp (same representation)
 
-template <int VS, int RS, int ORS, int RULE, bool REG, bool TRACE>
+template <int VS, int RS, int ORS, int RULE, bool REG, bool OUT>
 __global__ void __launch_bounds__(kSmallWarps * 32, small_min_blocks(RS, RULE))
 decode_small_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) float smsg[];
@@ -31,14 +31,16 @@ decode_small_kernel(const DecodeArgs a) {
         const int b = (int)(chunk - (unsigned long long)sblock * R);
         const int s0 = sblock * kChunk;
         const int s1 = min(a.io.batch, s0 + kChunk);
-        small_bp::run_chunk<VS, RS, ORS, RULE, REG, TRACE>(B, a.io, b, s0, s1, smc, wbase);
+        small_bp::run_chunk<VS, RS, ORS, RULE, REG, OUT>(B, a.io, b, s0, s1, smc, wbase);
     }
 }
 
 template <int VS, int RS, int ORS, int RULE, bool REG>
 cudaError_t launch_small_t(const DecodeArgs& a, cudaStream_t s, int sm_count) {
-    auto kern = a.io.c2v ? decode_small_kernel<VS, RS, ORS, RULE, REG, true>
-                         : decode_small_kernel<VS, RS, ORS, RULE, REG, false>;
+    // calls that ask for posteriors or the message trace take the kernel
+    // that writes them; the plain decode has no test for them in its loops
+    auto kern = (a.io.c2v || a.io.post) ? decode_small_kernel<VS, RS, ORS, RULE, REG, true>
+                                        : decode_small_kernel<VS, RS, ORS, RULE, REG, false>;
     const int warps = kSmallWarps;
     const size_t smem = (size_t)warps * small_bp::warp_floats(a.B.MP, VS, ORS) * sizeof(float);
     int per_sm = 0;

@@ -184,7 +184,7 @@ struct SmallLayout {
     std::vector<int> order;               // variable at position p
 };
 
-SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, uint64_t seed) {
+SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, int MP, uint64_t seed) {
     const int M = (int)src.size();
     constexpr int DVX = 8;
     std::vector<std::vector<std::pair<int, int>>> ve(n);  // (row, j), ascending row
@@ -218,6 +218,24 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, ui
     auto cell = [&](int v, int i) { return (posof[v] >> 5) * DVX + i; };
     for (int v = 0; v < n; ++v)
         for (int i = 0; i < (int)ve[v].size(); ++i) ++cnt[(size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second)];
+    // The kernel runs every edge position i of a step up to the step's
+    // largest degree; lanes with fewer edges (and the padding positions past
+    // n) read the warp's zero slot there, all at one address (a broadcast):
+    // one more access in the zero slot's bank, fixed because moves only swap
+    // variables of equal degree between steps.
+    {
+        const int zero_bank = (6 * MP) & 31;
+        for (int st = 0; st < steps; ++st) {
+            int dmin = 1 << 30, dmax = 0;
+            for (int l = 0; l < 32; ++l) {
+                const int pp = 32 * st + l;
+                const int d = pp < n ? (int)ve[L.order[pp]].size() : 0;
+                dmin = std::min(dmin, d);
+                dmax = std::max(dmax, d);
+            }
+            for (int i = dmin; i < dmax && i < DVX; ++i) ++cnt[((size_t)st * DVX + i) * 32 + zero_bank];
+        }
+    }
     // cost of a cell: its largest bank count (the wavefronts of the access)
     // first, then its colliding lane pairs, so that a move removing one
     // collision of several is rewarded before the largest count drops
@@ -648,7 +666,7 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
             const int extra = set_ptr[t + 1] - set_ptr[t];
             std::vector<int> src(m + extra);
             for (int r = 0; r < m + extra; ++r) src[r] = r < m ? r : set_rows[set_ptr[t] + (r - m)];
-            const SmallLayout L = small_layout(g, src, n, 0x5EEDull + (uint64_t)t);
+            const SmallLayout L = small_layout(g, src, n, MP, 0x5EEDull + (uint64_t)t);
             std::vector<int> posof(n);
             for (int p = 0; p < n; ++p) posof[L.order[p]] = p;
             std::vector<std::vector<uint16_t>> vs(n);
