@@ -654,7 +654,7 @@ def run_paper(args):
     print(json.dumps(line), flush=True)
 
 
-def run_wms(args):
+def wms_measure(steps: int, warmup: int, sample_clocks: bool = False):
     """One training step of differentiable weighted min-sum per bench step on
     [[144,12,12]] (R = 8 subtree representations, T = 25 unrolled flooding
     iterations, per-edge per-iteration weights and damping, checkpoint
@@ -705,16 +705,20 @@ def run_wms(args):
         if record:
             ev.append(e)
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         step(k, False)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
-        t0.record()
-        for k in range(args.steps):
-            step(args.warmup + k, True)
-        t1.record()
-        torch.cuda.synchronize()
+    clk = ClockSampler(0) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    t0.record()
+    for k in range(steps):
+        step(warmup + k, True)
+    t1.record()
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__(None, None, None)
     ms = t0.elapsed_time(t1)
     fwd = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
     bwd = statistics.mean(b.elapsed_time(c_) for _, b, c_ in ev)
@@ -722,9 +726,9 @@ def run_wms(args):
     upd = batch * T * E  # forward message updates per step (every edge of every representation)
     ck_bytes = batch * B.R * int(B.edges.max()) * 4 * ((T - 1) // ckpt)
     full_bytes = batch * B.R * int(B.edges.max()) * 4 * T
-    line = {
-        "metric": "training syndromes/s", "value": args.steps * batch / (ms / 1e3), "unit": "syndromes/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+    return {
+        "metric": "training syndromes/s", "value": steps * batch / (ms / 1e3), "unit": "syndromes/s",
+        "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "weighted min-sum training step: [[144,12,12]] R=8, T=25 unrolled iterations, "
                                "per-edge per-iteration weights + damping, checkpoint every 5, batch 4096, "
@@ -734,10 +738,54 @@ def run_wms(args):
         "workspace_bytes": ws_bytes, "message_bytes_checkpointed": ck_bytes,
         "message_bytes_without_checkpoints": full_bytes,
         "loss": float(loss.sum().item()),
-        "gpu_launches": args.steps * 8,
-        "clocks": clk.summary(),
+        "gpu_launches": steps * 8,
+        "clocks": clk.summary() if clk else None,
     }
-    print(json.dumps(line), flush=True)
+
+
+def run_wms(args):
+    """The weighted min-sum training step as its own JSON line."""
+    print(json.dumps(wms_measure(args.steps, args.warmup, sample_clocks=True)), flush=True)
+
+
+def bb72_measure(reps: int = 20):
+    """The small configuration: [[72,12,6]], X errors (BSC) p = 0.05 decoded
+    with H_Z, R = 4, 50 iterations, alpha = 0.625, 2000 seeded shots; the
+    decode call (BP + FWS) timed with CUDA events, averaged over `reps`
+    calls on the same syndromes (a 2000-shot launch is latency-bound)."""
+    import torch
+
+    from paper_2605_14170_gb300 import mbbp
+    from paper_2605_14170_gb300.inputs import named_code
+
+    dev = torch.device("cuda", 0)
+    c = named_code("bb72")
+    shots, n = 2000, c.n
+    B = mbbp.mbbp_build_bases(c.HZ, 4, 20260514)
+    L = mbbp.mbbp_logicals_build(c.HZ, c.HX)
+    W = (n + 31) // 32
+    ex = torch.empty((shots, W), dtype=torch.int32, device=dev)
+    mbbp.mbbp_sample_errors(n, shots, 0, 20260514, 0.05, mbbp.NOISE_BSC, ex)
+    syn = torch.empty((shots, B.m), dtype=torch.uint8, device=dev)
+    mbbp.mbbp_syndrome(B, ex, syn)
+    llr = torch.full((n,), float(np.log(0.95 / 0.05)), dtype=torch.float32, device=dev)
+    out = mbbp.decode(B, syn, llr, 50, ALPHA)
+    times = []
+    for _ in range(reps + 3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mbbp.mbbp_decode(B, syn, llr, 50, ALPHA, mbbp.RULE_NMS, out["e_hat"], out["conv"], out["success"],
+                         out["workspace"], iters_run=out["iters"], selected=out["selected"])
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times[3:])
+    cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+    mbbp.mbbp_judge(L, ex, out["e_hat"], None, cnt)
+    c3 = cnt.cpu().numpy()
+    return {"workload": "[[72,12,6]] BB, X errors (BSC) p=0.05 decoded with H_Z, R=4, 50 iters, alpha 0.625, "
+                        "2000 shots", "decode_ms": ms, "shots_per_s": shots / (ms / 1e3),
+            "failures": int(c3[1] + c3[2]), "shots": shots}
 
 
 def main():
@@ -908,11 +956,13 @@ def main():
 
     extra = None
     if rank == 0 and world == 1 and not args.no_extra:
-        # the other two decode configurations, measured on the same GPU after
-        # the headline's timed region: the mixed batch (3e5 shots, graph-
-        # replayed persistent launches vs per-code launches) and plain
-        # MBBP-LD on the length-882 GB code with R = 64
-        extra = {"mixed": mixed_measure(300_000, 5, 3), "gb882_r64_plain": gb882_measure(100_000)}
+        # the other configurations, measured on the same GPU after the
+        # headline's timed region: the mixed batch (3e5 shots, graph-replayed
+        # persistent launches vs per-code launches), plain MBBP-LD on the
+        # length-882 GB code with R = 64, the weighted min-sum training step
+        # and the small [[72,12,6]] decode
+        extra = {"mixed": mixed_measure(300_000, 5, 3), "gb882_r64_plain": gb882_measure(100_000),
+                 "wms_training": wms_measure(5, 3), "bb72_r4": bb72_measure()}
         extra["mixed"]["workload"] = MIXED_WORKLOAD
 
     cb = None
