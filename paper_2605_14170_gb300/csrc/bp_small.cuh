@@ -143,16 +143,16 @@ __device__ __forceinline__ float var_upd_step(char* smc, const uint4& d, float m
     return P[DM];
 }
 
+// The step's body by its largest degree: a chain of uniform tests, the
+// common case first (measured: a six-way switch compiled to slower branches,
+// 7.56 vs 8.63 M shots/s on the [[144,12,12]] workload).  Steps whose lanes
+// have at most 3 edges run the degree-3 body (the missing edges read the zero
+// slot, exactly as above).
 __device__ __forceinline__ float var_step(char* smc, int dmax, int deg, const uint4& d, float mu) {
-    switch (dmax) {
-        case 1: return var_upd_step<1>(smc, d, mu, deg);
-        case 2: return var_upd_step<2>(smc, d, mu, deg);
-        case 3: return var_upd_step<3>(smc, d, mu, deg);
-        case 4: return var_upd_step<4>(smc, d, mu, deg);
-        case 5: return var_upd_step<5>(smc, d, mu, deg);
-        case 6: return var_upd_step<6>(smc, d, mu, deg);
-        default: return mu;
-    }
+    if (dmax <= 3) return var_upd_step<3>(smc, d, mu, deg);
+    if (dmax == 4) return var_upd_step<4>(smc, d, mu, deg);
+    if (dmax == 5) return var_upd_step<5>(smc, d, mu, deg);
+    return var_upd_step<6>(smc, d, mu, deg);
 }
 
 // Decode shots [shot_begin, shot_end) on representation b.  smc is the
