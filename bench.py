@@ -55,7 +55,7 @@ EDGE_UPDATES_PER_CLK_SM = min(ALU_LANES / ALU_OPS, FMA_LANES / FMA_OPS, ISSUE_LA
 # of the current kernel (profiles/decode_small_kernel_bb144_r16.md: 7.326 MB
 # read + 3.3 KB written); set to None whenever the kernel changes until it is
 # captured again
-DRAM_BYTES_PER_SHOT = (7.325952e6 + 3.328e3) / 100000
+DRAM_BYTES_PER_SHOT = None
 WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
 
 

@@ -9,8 +9,9 @@
 // the shared-memory byte addresses of every variable's edges in ascending row
 // order of H^(t) and the variable degrees stay in registers, the rows of H as
 // bit masks over positions go to the warp's shared memory.  Variables are
-// visited in degree-sorted order (the lanes of a step mostly take the same
-// case of the degree switch); check messages leave the check pass pre-signed;
+// visited in degree-sorted order, 32 per step, and each step runs at the
+// largest degree among its lanes (no divergence); check messages leave the
+// check pass pre-signed;
 // the halting test H e = s runs on ballot-packed hard decisions, a row group
 // at a time.  The host places rows and variables (row index sigma(r), bank
 // rotation of edge position j) to spread the variable pass over the banks.
