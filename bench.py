@@ -52,10 +52,10 @@ ALU_OPS, FMA_OPS = 7, 3
 ALU_LANES, FMA_LANES, ISSUE_LANES = 64, 128, 128
 EDGE_UPDATES_PER_CLK_SM = min(ALU_LANES / ALU_OPS, FMA_LANES / FMA_OPS, ISSUE_LANES / OPS_PER_EDGE_UPDATE)
 # DRAM bytes per shot of the BP kernel: one ncu capture of a 100k-shot launch
-# of the current kernel (profiles/decode_small_kernel_bb144_r16.md: 7.326 MB
-# read + 3.3 KB written); set to None whenever the kernel changes until it is
+# of the current kernel (profiles/decode_small_kernel_bb144_r16.md: 7.304 MB
+# read + 1.8 KB written); set to None whenever the kernel changes until it is
 # captured again
-DRAM_BYTES_PER_SHOT = None
+DRAM_BYTES_PER_SHOT = (7.304192e6 + 1.792e3) / 100000
 WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
 
 
@@ -831,8 +831,10 @@ def main():
     n = code.n
     W = (n + 31) // 32
     S = args.shots
+    t_build = time.perf_counter()
     BZ = mbbp.mbbp_build_bases(code.HZ, R, SEED)       # X errors
     BX = mbbp.mbbp_build_bases(code.HX, R, SEED + 1)   # Z errors
+    t_build = time.perf_counter() - t_build
     LZ = mbbp.mbbp_logicals_build(code.HZ, code.HX)
     LX = mbbp.mbbp_logicals_build(code.HX, code.HZ)
     m = code.HZ.shape[0]
@@ -985,6 +987,7 @@ def main():
                        "l2": "inputs larger than L2 (per decode call: "
                              f"{S * m / 1e6:.0f} MB syndromes, {ws.numel() / 1e6:.0f} MB workspace, "
                              f"{S * n / 1e6:.0f} MB estimates)"},
+            "bases_build_s": t_build,
             "edge_updates_per_s": edge_updates / (ms / 1000.0),
             "edge_updates_per_shot": edge_updates / shots_total,
             "edge_updates_per_shot_dense_bound": 2 * R * float(np.mean(BZ.edges)) * ITERS,

@@ -4,12 +4,15 @@
 // argument checking for the launches.
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mbbp_internal.h"
@@ -214,10 +217,36 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, in
     for (int p = 0; p < n; ++p) posof[L.order[p]] = p;
     const int steps = (n + 31) / 32;
     std::vector<int> cnt((size_t)steps * DVX * 32, 0), mx((size_t)steps * DVX, 0);
+    // per cell, kept up to date on every count change: the number of banks
+    // holding each count, the largest count and the colliding lane pairs, so
+    // that a cell's cost is read in O(1) (the same values as counting its 32
+    // banks)
+    constexpr int kMaxCount = 40;
+    std::vector<int> hist((size_t)steps * DVX * (kMaxCount + 1), 0), top((size_t)steps * DVX, 0),
+        pairs((size_t)steps * DVX, 0);
+    for (int c = 0; c < steps * DVX; ++c) hist[(size_t)c * (kMaxCount + 1)] = 32;
+    auto inc = [&](size_t idx) {
+        const size_t c = idx >> 5;
+        const int q = cnt[idx]++;
+        int* h = &hist[c * (kMaxCount + 1)];
+        --h[q];
+        ++h[q + 1];
+        pairs[c] += q;
+        if (q + 1 > top[c]) top[c] = q + 1;
+    };
+    auto dec = [&](size_t idx) {
+        const size_t c = idx >> 5;
+        const int q = cnt[idx]--;
+        int* h = &hist[c * (kMaxCount + 1)];
+        --h[q];
+        ++h[q - 1];
+        pairs[c] -= q - 1;
+        if (q == top[c] && h[q] == 0) top[c] = q - 1;
+    };
     auto bank = [&](int r, int j) { return (L.sigma[r] + slot_rot(L.slot[r][j])) & 31; };
     auto cell = [&](int v, int i) { return (posof[v] >> 5) * DVX + i; };
     for (int v = 0; v < n; ++v)
-        for (int i = 0; i < (int)ve[v].size(); ++i) ++cnt[(size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second)];
+        for (int i = 0; i < (int)ve[v].size(); ++i) inc((size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second));
     // The kernel runs every edge position i of a step up to the step's
     // largest degree; lanes with fewer edges (and the padding positions past
     // n) read the warp's zero slot there, all at one address (a broadcast):
@@ -233,32 +262,24 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, in
                 dmin = std::min(dmin, d);
                 dmax = std::max(dmax, d);
             }
-            for (int i = dmin; i < dmax && i < DVX; ++i) ++cnt[((size_t)st * DVX + i) * 32 + zero_bank];
+            for (int i = dmin; i < dmax && i < DVX; ++i) inc(((size_t)st * DVX + i) * 32 + zero_bank);
         }
     }
     // cost of a cell: its largest bank count (the wavefronts of the access)
     // first, then its colliding lane pairs, so that a move removing one
     // collision of several is rewarded before the largest count drops
-    auto remax = [&](int c) {
-        int x = 0, pairs = 0;
-        for (int k = 0; k < 32; ++k) {
-            const int q = cnt[(size_t)c * 32 + k];
-            x = std::max(x, q);
-            pairs += q * (q - 1) / 2;
-        }
-        mx[c] = x * 1024 + pairs;
-    };
+    auto remax = [&](int c) { mx[c] = top[c] * 1024 + pairs[c]; };
     long total = 0;
     for (int c = 0; c < steps * DVX; ++c) { remax(c); total += mx[c]; }
     std::vector<int> best_sigma = L.sigma, best_order = L.order;
     std::vector<std::array<int, 6>> best_slot = L.slot;
-    long best = total;
+    long best = LONG_MAX;  // none yet
     uint64_t rs = seed;
     auto rnd = [&]() { rs += 0x9E3779B97F4A7C15ULL; uint64_t z = rs;
                        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
                        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL; return z ^ (z >> 31); };
     std::vector<int> cells;
-    const int iters = 100000;
+    const int iters = 1000000;
     for (int it = 0; it < iters; ++it) {
         const double T = 0.6 * (1.0 - (double)it / iters) + 0.02;
         cells.clear();
@@ -277,11 +298,11 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, in
             if (cb != ca) cells.push_back(cb);
             for (int c : cells) before += mx[c];
             auto swap_slots = [&]() {
-                --cnt[(size_t)ca * 32 + bank(r, ja)];
-                --cnt[(size_t)cb * 32 + bank(r, jb)];
+                dec((size_t)ca * 32 + bank(r, ja));
+                dec((size_t)cb * 32 + bank(r, jb));
                 std::swap(L.slot[r][ja], L.slot[r][jb]);
-                ++cnt[(size_t)ca * 32 + bank(r, ja)];
-                ++cnt[(size_t)cb * 32 + bank(r, jb)];
+                inc((size_t)ca * 32 + bank(r, ja));
+                inc((size_t)cb * 32 + bank(r, jb));
             };
             swap_slots();
             for (int c : cells) { remax(c); after += mx[c]; }
@@ -302,12 +323,12 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, in
             std::sort(cells.begin(), cells.end());
             cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
             for (int c : cells) before += mx[c];
-            const std::vector<int> keep = cells;
+            const std::vector<int>& keep = cells;  // not changed below
             for (int rr : {a, b})
-                for (auto& e : re[rr]) --cnt[(size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second)];
+                for (auto& e : re[rr]) dec((size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second));
             std::swap(L.sigma[a], L.sigma[b]);
             for (int rr : {a, b})
-                for (auto& e : re[rr]) ++cnt[(size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second)];
+                for (auto& e : re[rr]) inc((size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second));
             for (int c : keep) { remax(c); after += mx[c]; }
             const long d = after - before;
             const double u = (double)(rnd() >> 11) * (1.0 / 9007199254740992.0);
@@ -315,10 +336,10 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, in
                 total += d;
             } else {
                 for (int rr : {a, b})
-                    for (auto& e : re[rr]) --cnt[(size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second)];
+                    for (auto& e : re[rr]) dec((size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second));
                 std::swap(L.sigma[a], L.sigma[b]);
                 for (int rr : {a, b})
-                    for (auto& e : re[rr]) ++cnt[(size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second)];
+                    for (auto& e : re[rr]) inc((size_t)cell(e.first, e.second) * 32 + bank(rr, ve[e.first][e.second].second));
                 for (int c : keep) remax(c);
             }
         } else {
@@ -334,16 +355,16 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, in
             std::sort(cells.begin(), cells.end());
             cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
             for (int c : cells) before += mx[c];
-            const std::vector<int> keep = cells;
+            const std::vector<int>& keep = cells;  // not changed below
             auto swap_vars = [&]() {
                 for (int v : {va, vb})
                     for (int i = 0; i < (int)ve[v].size(); ++i)
-                        --cnt[(size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second)];
+                        dec((size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second));
                 std::swap(L.order[posof[va]], L.order[posof[vb]]);
                 std::swap(posof[va], posof[vb]);
                 for (int v : {va, vb})
                     for (int i = 0; i < (int)ve[v].size(); ++i)
-                        ++cnt[(size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second)];
+                        inc((size_t)cell(v, i) * 32 + bank(ve[v][i].first, ve[v][i].second));
             };
             swap_vars();
             for (int c : keep) { remax(c); after += mx[c]; }
@@ -356,16 +377,21 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, in
                 for (int c : keep) remax(c);
             }
         }
-        if (total < best) {
+        // the best state of the cold half of the schedule (the hot half
+        // only wanders; snapshotting it would copy the layout thousands of
+        // times)
+        if (2 * it >= iters && total < best) {
             best = total;
             best_sigma = L.sigma;
             best_slot = L.slot;
             best_order = L.order;
         }
     }
-    L.sigma = best_sigma;
-    L.slot = best_slot;
-    L.order = best_order;
+    if (best < total) {  // else the final state is the best one seen
+        L.sigma = best_sigma;
+        L.slot = best_slot;
+        L.order = best_order;
+    }
     return L;
 }
 
@@ -662,11 +688,30 @@ mbbp_status build_impl(const uint8_t* H, int m, int n, int R, const int32_t* set
         rinfo2.assign((size_t)R * MP, 0);
         hmask2.assign((size_t)R * VS * ORS * 32, 0);
         sedge.assign((size_t)R * 6 * MP, -1);
+        // the bank placements of the R representations are independent:
+        // anneal them on the host's cores
+        std::vector<SmallLayout> layouts(R);
+        {
+            const int nth = std::max(1, std::min(R, (int)std::thread::hardware_concurrency()));
+            std::atomic<int> next{0};
+            auto worker = [&]() {
+                for (int t = next++; t < R; t = next++) {
+                    const int extra = set_ptr[t + 1] - set_ptr[t];
+                    std::vector<int> src(m + extra);
+                    for (int r = 0; r < m + extra; ++r) src[r] = r < m ? r : set_rows[set_ptr[t] + (r - m)];
+                    layouts[t] = small_layout(g, src, n, MP, 0x5EEDull + (uint64_t)t);
+                }
+            };
+            std::vector<std::thread> pool;
+            for (int i = 1; i < nth; ++i) pool.emplace_back(worker);
+            worker();
+            for (auto& th : pool) th.join();
+        }
         for (int t = 0; t < R; ++t) {
             const int extra = set_ptr[t + 1] - set_ptr[t];
             std::vector<int> src(m + extra);
             for (int r = 0; r < m + extra; ++r) src[r] = r < m ? r : set_rows[set_ptr[t] + (r - m)];
-            const SmallLayout L = small_layout(g, src, n, MP, 0x5EEDull + (uint64_t)t);
+            const SmallLayout& L = layouts[t];
             std::vector<int> posof(n);
             for (int p = 0; p < n; ++p) posof[L.order[p]] = p;
             std::vector<std::vector<uint16_t>> vs(n);
