@@ -437,6 +437,8 @@ def gb882_measure(shots: int, steps: int = 1, warmup: int = 1, p_list=None, wms:
         if wms:
             w, g = mbbp.wms_params(B, 25, alpha=ALPHA, device=dev)
             o2 = {k: torch.empty_like(v) for k, v in out.items()}
+            o2["workspace"] = torch.empty(mbbp.mbbp_wms_decode_workspace_size(B, shots, 25), dtype=torch.uint8,
+                                          device=dev)
             wt = []
             for k in range(warmup + steps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

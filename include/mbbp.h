@@ -381,9 +381,17 @@ mbbp_status mbbp_wms_backward(const mbbp_bases* B, int batch, const uint8_t* syn
                               float* gw,
                               float* gg, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Workspace of mbbp_wms_decode: mbbp_decode's, then a copy of w and g
+ * rearranged into the kernel's message layout, 8 bytes per slot and
+ * R * T * K * MP slots: K the smallest of 6, 8, 12 not below any row or
+ * column weight of the H^(t), MP the rows of the largest H^(t) rounded up to
+ * a multiple of 32.  Returns 0 for a NULL handle, batch < 0 or T < 1. */
+size_t mbbp_wms_decode_workspace_size(const mbbp_bases* B, int batch, int T);
+
 /* Algorithm 1 with WMS as the BP of every representation: the halting rule
  * after every iteration (up to `iters`; iterations past T use the weights of
- * iteration T), then FWS.  Outputs and workspace as mbbp_decode. */
+ * iteration T), then FWS.  Outputs as mbbp_decode; the workspace holds at
+ * least mbbp_wms_decode_workspace_size(B, batch, T) bytes. */
 mbbp_status mbbp_wms_decode(const mbbp_bases* B, int batch, const uint8_t* syndromes, const float* llr,
                             int llr_stride, int iters, int T, const float* w, const float* g,
                             uint8_t* e_hat, uint8_t* conv, uint16_t* iters_run, uint8_t* success,

@@ -1462,6 +1462,13 @@ mbbp_status wms_check(const mbbp_bases* B, int batch, int T, int ckpt) {
 
 }  // namespace
 
+size_t mbbp_wms_decode_workspace_size(const mbbp_bases* B, int batch, int T) {
+    if (!B || batch < 0 || T < 1) return 0;
+    // mbbp_decode's workspace, then (w, g) of every representation and
+    // iteration in the message layout
+    return mbbp_decode_workspace_size(B, batch) + align256((size_t)B->R * T * B->dev.DC * B->MP * 8);
+}
+
 size_t mbbp_wms_workspace_size(const mbbp_bases* B, int batch, int T, int ckpt) {
     if (!B || batch < 0 || T < 1 || ckpt < 1) return 0;
     const size_t nckpt = (size_t)((T - 1) / ckpt);
@@ -1569,7 +1576,8 @@ mbbp_status mbbp_wms_decode(const mbbp_bases* B, int batch, const uint8_t* syndr
     if (!syndromes || !llr || !w || !g || !e_hat || !conv || !success || !workspace)
         return fail(MBBP_E_INVALID, "mbbp_wms_decode: NULL buffer");
     if (llr_stride != 0 && llr_stride < B->n) return fail(MBBP_E_INVALID, "llr_stride must be 0 or >= n");
-    if (workspace_bytes < mbbp_decode_workspace_size(B, batch)) return fail(MBBP_E_INVALID, "workspace too small");
+    if (workspace_bytes < mbbp_wms_decode_workspace_size(B, batch, T))
+        return fail(MBBP_E_INVALID, "workspace too small");
     WmsArgs a{};
     a.B = B->dev;
     a.synd = syndromes;
@@ -1588,8 +1596,12 @@ mbbp_status mbbp_wms_decode(const mbbp_bases* B, int batch, const uint8_t* syndr
     a.conv = conv;
     a.iters_run = iters_run;
     a.total_items = (unsigned long long)batch * B->R;
+    // the parameters in the message layout follow the decode workspace
+    float2* wg = reinterpret_cast<float2*>(static_cast<char*>(workspace) + mbbp_decode_workspace_size(B, batch));
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(a.counter, 0, 8, s);
+    if (e == cudaSuccess) e = launch_wms_pack(a, wg, s, B->sm_count);
+    a.wg = wg;
     if (e == cudaSuccess) e = launch_wms(a, false, s, B->sm_count);
     if (e != cudaSuccess) return cuda_fail(e, "mbbp_wms_decode");
     FwsArgs f{};

@@ -207,6 +207,7 @@ struct WmsArgs {
     float* gw;                  // [R][T][E]
     float* gg;
     int decode, iters;          // decode mode: halting rule, candidates
+    const float2* wg;           // decode mode: (w, g) in the message layout [R][T][DC][MP], or null
     uint32_t* cand;
     uint8_t* conv;
     uint16_t* iters_run;
@@ -218,6 +219,8 @@ constexpr int kWmsMaxWarps = 152 * 16;  // warps of the backward grid (segment b
 // (then it needs no per-warp segment buffers in the workspace).
 bool wms_states_in_smem(const DevBases& B, int ckpt);
 cudaError_t launch_wms(const WmsArgs& a, bool backward, cudaStream_t s, int sm_count);
+// Fills a.wg-style packed parameters from a.w / a.g (a.T iterations).
+cudaError_t launch_wms_pack(const WmsArgs& a, float2* wg, cudaStream_t s, int sm_count);
 cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, size_t count, float lr, float b1,
                         float b2, float eps, int step, float lo, float hi, cudaStream_t s);
 

@@ -30,7 +30,7 @@ constexpr int kWmsWarps = 8;       // largest block (warps); the launch picks th
 constexpr int kWmsStateWarps = 4;  // warps whose segment states must fit for the shared-memory path
 
 struct WmsLayout {
-    int S, npad, ehpad;
+    int S, npad;
     size_t fwd_bytes, bwd_bytes;
 };
 
@@ -38,9 +38,8 @@ __host__ __device__ inline WmsLayout wms_layout(int DC, int MP, int n, int ckpt)
     WmsLayout L;
     L.S = DC * MP;
     L.npad = (n + 4) & ~3;
-    L.ehpad = (n + 1 + 15) & ~15;
-    // forward: m, q (S each), mu, post (npad each), hard decision bytes
-    L.fwd_bytes = (size_t)(2 * L.S + 2 * L.npad) * 4 + L.ehpad;
+    // forward: m, q (S each), mu, post (npad each: n, a padding column)
+    L.fwd_bytes = (size_t)(2 * L.S + 2 * L.npad) * 4;
     // backward: q, gm (updated in place from dL/dm^(t) to dL/dm^(t-1)), gq
     // (S each), mu (npad); the segment's states follow in shared memory or
     // live in a per-warp global buffer of ckpt * S floats
@@ -127,10 +126,12 @@ __device__ __forceinline__ void wms_var_pass(const DevBases& B, int b, const uin
 }
 
 // One WMS check pass: m <- g m + (1 - g) w S mn(q).  wt, gt: parameters of
-// this iteration for representation b ([E] in row-major edge order).  With G
-// warps per item the thread with group index gt takes rows gt, gt + 32 G,
-// ...; bit k of sb is the syndrome bit of its k-th row.
-template <int DC, int G = 1>
+// this iteration for representation b ([E] in row-major edge order); or,
+// with SLOT, wt points at the iteration's (w, g) pairs in the message layout
+// (pair of edge j of row r at float2 index j * MP + r: one coalesced load
+// per edge).  With G warps per item the thread with group index gt takes
+// rows gt, gt + 32 G, ...; bit k of sb is the syndrome bit of its k-th row.
+template <int DC, int G = 1, bool SLOT = false>
 __device__ __forceinline__ void wms_check_pass(const DevBases& B, int b, const uint32_t* rinfo,
                                                int Mb, uint32_t sb, const float* q, float* m,
                                                const float* wt, const float* gt) {
@@ -142,7 +143,7 @@ __device__ __forceinline__ void wms_check_pass(const DevBases& B, int b, const u
         const int r = lane + GT * k;
         if (r >= Mb) continue;
         const int deg = B.regular ? DC : (int)((__ldg(rinfo + r) >> 16) & 0xffu);
-        const int e0 = __ldg(rp + r);
+        const int e0 = SLOT ? 0 : __ldg(rp + r);
         float qq[DC];
 #pragma unroll
         for (int j = 0; j < DC; ++j) qq[j] = (j < deg) ? q[j * MP + r] : MBBP_LMAX;
@@ -166,8 +167,16 @@ __device__ __forceinline__ void wms_check_pass(const DevBases& B, int b, const u
             if (j >= deg) continue;
             const float mn = (j == DC - 1) ? pre[j] : (j == 0 ? fminf(MBBP_LMAX, suf[0]) : fminf(pre[j], suf[j]));
             const float smn = __uint_as_float(__float_as_uint(mn) ^ ((sx ^ __float_as_uint(qq[j])) & 0x80000000u));
-            const float c = __fmul_rn(__ldg(wt + e0 + j), smn);
-            const float gg = __ldg(gt + e0 + j);
+            float wj, gg;
+            if constexpr (SLOT) {
+                const float2 p = __ldg(reinterpret_cast<const float2*>(wt) + j * MP + r);
+                wj = p.x;
+                gg = p.y;
+            } else {
+                wj = __ldg(wt + e0 + j);
+                gg = __ldg(gt + e0 + j);
+            }
+            const float c = __fmul_rn(wj, smn);
             const float mo = m[j * MP + r];
             m[j * MP + r] = __fadd_rn(__fmul_rn(gg, mo), __fmul_rn(__fsub_rn(1.0f, gg), c));
         }
@@ -182,10 +191,13 @@ __device__ __forceinline__ float bce_neg_sigmoid(float post, int e) {
 // G warps decode each item together (G = 1: one warp per item; G > 1 for
 // codes whose two message arrays per item, not registers, limit the resident
 // warps).  Group g of the block uses named barrier 1 + g; the arithmetic of
-// every row and variable is the same whatever G.
-template <int DC, int DV, int G = 1>
-__global__ void __launch_bounds__(kWmsWarps * 32)
-wms_forward_kernel(const WmsArgs a) {
+// every row and variable is the same whatever G.  The hard decisions are the
+// posteriors' sign bits (no posterior is -0: it is a sum that starts from
+// mu, and mu enters as llr + 0).  The arguments come by value (taken by
+// reference from the kernel's parameter, the decode on a length-882 code
+// measured 5% slower).
+template <int DC, int DV, int G>
+__device__ __forceinline__ void wms_forward_items(const WmsArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long group_item[kWmsWarps];
     __shared__ float group_part[kWmsWarps];
@@ -200,8 +212,7 @@ wms_forward_kernel(const WmsArgs a) {
     float* m = reinterpret_cast<float*>(smem + grp * L.fwd_bytes);
     float* q = m + L.S;
     float* mu = q + L.S;
-    float* post = mu + L.npad;
-    uint8_t* eh = reinterpret_cast<uint8_t*>(post + L.npad);
+    float* post = mu + L.npad;  // post[n] = +0: the padding column of hcol
     const int orow_steps = (B.mpad + GT - 1) / GT;
     const int row_steps = (MP + GT - 1) / GT;
     // H's columns for the halting test, once per block
@@ -238,9 +249,8 @@ wms_forward_kernel(const WmsArgs a) {
             const float x = __fadd_rn(__ldg(llr + v), 0.0f);  // -0 -> +0 (sign bits decide the check rule)
             mu[v] = x;
             post[v] = x;
-            eh[v] = (x < 0.f) ? 1 : 0;
         }
-        if (lane == 0) eh[n] = 0;
+        if (lane == 0) post[n] = 0.0f;
         for (int i = lane; i < L.S; i += GT) m[i] = 0.0f;
         uint32_t sb = 0;
         for (int k = 0; k < row_steps; ++k) {
@@ -260,15 +270,18 @@ wms_forward_kernel(const WmsArgs a) {
         const int iters = a.decode ? a.iters : a.T;
         for (int it = 0;; ++it) {
             if (a.decode) {
+                // the first row group decides most unconverged iterations,
+                // so the other groups are tested only if it passed
                 bool ok = true;
                 for (int k = 0; k < orow_steps; ++k) {
                     const int r = lane + GT * k;
                     if (r < m_rows) {
                         uint32_t par = (sb >> k) & 1u;
 #pragma unroll
-                        for (int j = 0; j < DC; ++j) par ^= eh[hcol_s[j * B.mpad + r]];
+                        for (int j = 0; j < DC; ++j) par ^= __float_as_uint(post[hcol_s[j * B.mpad + r]]) >> 31;
                         ok = ok && (par == 0u);
                     }
+                    if (k == 0 && orow_steps > 1 && !generic_bp::gall<G>(ok, bar)) break;  // group-uniform
                 }
                 if (generic_bp::gall<G>(ok, bar)) {
                     conv = true;
@@ -281,16 +294,19 @@ wms_forward_kernel(const WmsArgs a) {
                 break;
             }
             const int tp = min(it, a.T - 1);  // iterations past T reuse the last weights
-            const float* wt = a.w + ((size_t)b * a.T + tp) * a.E;
-            const float* gt = a.g + ((size_t)b * a.T + tp) * a.E;
-            wms_check_pass<DC, G>(B, b, rinfo, Mb, sb, q, m, wt, gt);
+            if (a.wg) {
+                const float2* wgt = a.wg + ((size_t)b * a.T + tp) * DC * MP;
+                wms_check_pass<DC, G, true>(B, b, rinfo, Mb, sb, q, m, reinterpret_cast<const float*>(wgt),
+                                            nullptr);
+            } else {
+                const float* wt = a.w + ((size_t)b * a.T + tp) * a.E;
+                const float* gt = a.g + ((size_t)b * a.T + tp) * a.E;
+                wms_check_pass<DC, G>(B, b, rinfo, Mb, sb, q, m, wt, gt);
+            }
             generic_bp::gsync<G>(bar);
             wms_var_pass<DV, G>(B, b, vd, m, q, mu, post);
             generic_bp::gsync<G>(bar);
-            if (a.decode) {
-                for (int v = lane; v < n; v += GT) eh[v] = (post[v] < 0.f) ? 1 : 0;
-                generic_bp::gsync<G>(bar);
-            } else {
+            if (!a.decode) {
                 if (a.ckpt_buf && (it + 1) % a.ckpt == 0 && it + 1 < a.T) {
                     float* dst = a.ckpt_buf + ((size_t)item * a.nckpt + ((it + 1) / a.ckpt - 1)) * L.S;
                     for (int i = lane; i < L.S; i += GT) dst[i] = m[i];
@@ -308,7 +324,7 @@ wms_forward_kernel(const WmsArgs a) {
             const int wl = lane & 31;
             for (int w = wig; w < W; w += G) {
                 const int v = 32 * w + wl;
-                const uint32_t word = __ballot_sync(kFull, v < n && eh[v]);
+                const uint32_t word = __ballot_sync(kFull, v < n && post[v] < 0.f);
                 if (wl == 0) a.cand[item * W + w] = word;
             }
             if (lane == 0) {
@@ -333,6 +349,20 @@ wms_forward_kernel(const WmsArgs a) {
         }
         generic_bp::gsync<G>(bar);
     }
+}
+
+// One warp per item: the compiler's own register choice.
+template <int DC, int DV>
+__global__ void __launch_bounds__(kWmsWarps * 32) wms_forward_warp_kernel(const WmsArgs a) {
+    wms_forward_items<DC, DV, 1>(a);
+}
+
+// G > 1 warps per item: registers for three 8-warp blocks per SM, the
+// residency that the message areas allow for the codes that take G > 1
+// (without the bound the compiler stops at 64 registers and spills).
+template <int DC, int DV, int G>
+__global__ void __launch_bounds__(kWmsWarps * 32, 3) wms_forward_kernel(const WmsArgs a) {
+    wms_forward_items<DC, DV, G>(a);
 }
 
 // SMEM_ST: the segment's recomputed states sit in shared memory after the
@@ -558,6 +588,33 @@ wms_backward_kernel(const WmsArgs a) {
     }
 }
 
+// Decode mode: the parameters of every (representation, iteration) in the
+// message layout, w and g side by side: wg[((b T + t) DC + j) MP + r] is the
+// (w, g) of edge j of row r of H^(b) at iteration t, zeros where the row has
+// no edge j, so that the check pass reads one coalesced float2 per edge.
+template <int DC>
+__global__ void wms_pack_kernel(const WmsArgs a, float2* __restrict__ wg) {
+    const DevBases& B = a.B;
+    const int MP = B.MP;
+    const size_t total = (size_t)B.R * a.T * MP;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i % MP);
+        const size_t bt = i / MP;  // b T + t
+        const int b = (int)(bt / a.T);
+        int deg = 0, e0 = 0;
+        if (r < __ldg(B.rows + b)) {
+            deg = B.regular ? DC : (int)((__ldg(B.rowinfo + (size_t)b * MP + r) >> 16) & 0xffu);
+            e0 = __ldg(B.rowptr + (size_t)b * MP + r);
+        }
+        const float* wt = a.w + bt * a.E + e0;
+        const float* gt = a.g + bt * a.E + e0;
+#pragma unroll
+        for (int j = 0; j < DC; ++j)
+            wg[(bt * DC + j) * MP + r] = (j < deg) ? make_float2(__ldg(wt + j), __ldg(gt + j)) : make_float2(0.f, 0.f);
+    }
+}
+
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ grad, float* __restrict__ m1,
                             float* __restrict__ m2, size_t count, float lr, float b1, float b2, float eps,
                             float c1, float c2, float lo, float hi) {
@@ -580,7 +637,10 @@ cudaError_t launch_forward_g(const WmsArgs& a, size_t fixed, size_t per_item, in
     unsigned long long want = (a.total_items + groups - 1) / groups;
     unsigned long long grid = (unsigned long long)per_sm * sm_count;
     if (want < grid) grid = want;
-    wms_forward_kernel<K, K, G><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    if constexpr (G == 1)
+        wms_forward_warp_kernel<K, K><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    else
+        wms_forward_kernel<K, K, G><<<(unsigned)grid, warps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -595,7 +655,7 @@ cudaError_t launch_wms_t(const WmsArgs& a, bool backward, cudaStream_t s, int sm
         // half again as many warps as the best smaller one
         if (L.fwd_bytes > 200 * 1024) return cudaErrorInvalidConfiguration;
         const size_t fixed = (size_t)((K * a.B.mpad * 2 + 15) & ~15);
-        const void* kerns[3] = {reinterpret_cast<const void*>(wms_forward_kernel<K, K, 1>),
+        const void* kerns[3] = {reinterpret_cast<const void*>(wms_forward_warp_kernel<K, K>),
                                 reinterpret_cast<const void*>(wms_forward_kernel<K, K, 2>),
                                 reinterpret_cast<const void*>(wms_forward_kernel<K, K, 4>)};
         int best_g = -1, best_w = 0, best_b = 0;
@@ -669,6 +729,18 @@ cudaError_t launch_wms(const WmsArgs& a, bool backward, cudaStream_t s, int sm_c
     if (a.B.DC == 8) return launch_wms_t<8>(a, backward, s, sm_count);
     if (a.B.DC == 12) return launch_wms_t<12>(a, backward, s, sm_count);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_wms_pack(const WmsArgs& a, float2* wg, cudaStream_t s, int sm_count) {
+    const size_t total = (size_t)a.B.R * a.T * a.B.MP;
+    if (total == 0) return cudaSuccess;
+    size_t grid = (total + 255) / 256;
+    if (grid > (size_t)sm_count * 8) grid = (size_t)sm_count * 8;
+    if (a.B.DC == 6) wms_pack_kernel<6><<<(unsigned)grid, 256, 0, s>>>(a, wg);
+    else if (a.B.DC == 8) wms_pack_kernel<8><<<(unsigned)grid, 256, 0, s>>>(a, wg);
+    else if (a.B.DC == 12) wms_pack_kernel<12><<<(unsigned)grid, 256, 0, s>>>(a, wg);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, size_t count, float lr, float b1,

@@ -103,6 +103,7 @@ _sig = {
                                    C.c_float, C.c_int, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_wms_backward": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp,
                                     C.c_float, C.c_int, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "mbbp_wms_decode_workspace_size": (C.c_size_t, [_vp, C.c_int, C.c_int]),
     "mbbp_wms_decode": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp,
                                   _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "mbbp_adam_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_size_t, C.c_float, C.c_float, C.c_float,
@@ -539,6 +540,10 @@ def mbbp_wms_backward(B, syndromes, llr, T, w, g, ckpt, etrue, scale, posterior,
         _out(workspace, torch.uint8, "workspace", 0, dev), workspace.numel(), _stream(stream)), "mbbp_wms_backward")
 
 
+def mbbp_wms_decode_workspace_size(B: Bases, batch: int, T: int) -> int:
+    return int(_lib.mbbp_wms_decode_workspace_size(B.handle, batch, T))
+
+
 def mbbp_wms_decode(B, syndromes, llr, iters, T, w, g, e_hat, conv, success, workspace, iters_run=None,
                     selected=None, stream=None) -> None:
     import torch
@@ -570,7 +575,7 @@ def wms_decode(B, syndromes, llr, iters, w, g) -> dict:
            "iters": torch.empty((batch, B.R), dtype=torch.int16, device=dev),
            "success": torch.empty((batch,), dtype=torch.uint8, device=dev),
            "selected": torch.empty((batch,), dtype=torch.int16, device=dev)}
-    ws = torch.empty(mbbp_decode_workspace_size(B, batch), dtype=torch.uint8, device=dev)
+    ws = torch.empty(mbbp_wms_decode_workspace_size(B, batch, w.shape[1]), dtype=torch.uint8, device=dev)
     mbbp_wms_decode(B, syndromes, llr, iters, w.shape[1], w, g, out["e_hat"], out["conv"], out["success"], ws,
                     iters_run=out["iters"], selected=out["selected"])
     return out

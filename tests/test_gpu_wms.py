@@ -1,6 +1,9 @@
 """Differentiable weighted min-sum (WMS) on the GPU against the oracle.
 
 * w == alpha, g == 0: mbbp_wms_decode equals mbbp_decode bit for bit;
+* with a weight and damping of its own on every edge and iteration,
+  mbbp_wms_decode's halting iterations, flags and candidates equal those of
+  the FP64 oracle's posteriors;
 * forward posteriors within 1e-4 relative of the FP64 oracle;
 * the hand-written adjoint (mbbp_wms_backward) within 1e-3 relative of the
   oracle's FP64 adjoint and of FP64 central finite differences;
@@ -73,6 +76,86 @@ def test_wms_with_alpha_weights_is_normalized_min_sum():
     ref = mbbp.decode(B, s, llr, 60, 0.625)
     for key in ("e_hat", "conv", "iters", "success", "selected"):
         assert torch.equal(got[key], ref[key]), key
+
+
+def _irregular_H(seed, m=30, n=60):
+    """Rows of weight 3..6, columns of weight 1..4: H^(t) rows of several
+    degrees (the kernels' non-regular paths)."""
+    rng = np.random.default_rng(seed)
+    H = np.zeros((m, n), np.uint8)
+    H[np.arange(n) % m, np.arange(n)] = 1
+    for r in range(m):
+        want = int(rng.integers(3, 7))
+        free = [v for v in rng.permutation(n) if H[r, v] == 0 and H[:, v].sum() < 4]
+        for v in free[:max(0, want - int(H[r].sum()))]:
+            H[r, v] = 1
+    return H
+
+
+@pytest.mark.parametrize("code,R,shots", [("bb72", 4, 16), ("irregular", 4, 16), ("gb882", 64, 3)])
+def test_wms_decode_with_learned_weights_matches_oracle(code, R, shots):
+    """mbbp_wms_decode with a different weight and damping on every edge and
+    iteration (T = 6, 10 iterations: the last four reuse the weights of
+    iteration 6) against the oracle: for every (shot, representation) the
+    FP64 weighted min-sum posteriors after t = 0, 1, ... iterations give the
+    halting iteration, the flag and the candidate.  Items whose posteriors
+    come within 3e-4 of 0 (where FP32 rounding may decide differently; the
+    forward test bounds the FP32 posteriors' error by 1e-4) are not
+    compared: a few percent of them on the length-882 code."""
+    import torch
+    from paper_2605_14170_gb300 import mbbp
+    T, iters = 6, 10
+    H = _irregular_H(11) if code == "irregular" else named_code(code).HZ
+    m, n = H.shape
+    ex, _ = oracle.sample(7, 0, shots, n, 0.06, "depolarizing")
+    s = oracle.syndrome(H, ex)
+    B = mbbp.mbbp_build_bases(H, R, 7)
+    rng = np.random.default_rng(7)
+    mu = rng.uniform(1.0, 3.0, n).astype(np.float32)
+    E = int(B.edges.max())
+    w = rng.uniform(0.4, 1.0, (R, T, E)).astype(np.float32)
+    g = rng.uniform(0.0, 0.5, (R, T, E)).astype(np.float32)
+    dev = torch.device("cuda:0")
+    W = (n + 31) // 32
+    s_t, mu_t = torch.from_numpy(s).to(dev), torch.from_numpy(mu).to(dev)
+    w_t, g_t = torch.from_numpy(w).to(dev), torch.from_numpy(g).to(dev)
+    out = {"e_hat": torch.empty((shots, n), dtype=torch.uint8, device=dev),
+           "conv": torch.empty((shots, R), dtype=torch.uint8, device=dev),
+           "iters": torch.empty((shots, R), dtype=torch.int16, device=dev),
+           "success": torch.empty((shots,), dtype=torch.uint8, device=dev),
+           "selected": torch.empty((shots,), dtype=torch.int16, device=dev)}
+    ws = torch.empty(mbbp.mbbp_wms_decode_workspace_size(B, shots, T), dtype=torch.uint8, device=dev)
+    assert ws.numel() >= mbbp.mbbp_decode_workspace_size(B, shots) + 8 * R * T * E
+    with pytest.raises(mbbp.MBBPError):
+        mbbp.mbbp_wms_decode(B, s_t, mu_t, iters, T, w_t, g_t, out["e_hat"], out["conv"], out["success"],
+                             ws[:mbbp.mbbp_decode_workspace_size(B, shots)])
+    mbbp.mbbp_wms_decode(B, s_t, mu_t, iters, T, w_t, g_t, out["e_hat"], out["conv"], out["success"], ws,
+                         iters_run=out["iters"], selected=out["selected"])
+    torch.cuda.synchronize()
+    cand = ws[:shots * R * W * 4].view(torch.int32).cpu().numpy().reshape(shots, R, W).view(np.uint32)
+    conv, its = out["conv"].cpu().numpy(), out["iters"].cpu().numpy()
+    mu64 = mu.astype(np.float64)
+    compared = 0
+    for shot in range(shots):
+        for b in range(R):
+            Ht, st, wb, gb, _ = _oracle_item(H, B, s, mu64, w.astype(np.float64), g.astype(np.float64), ex, shot, b, 1.0)
+            wext = np.concatenate([wb, np.repeat(wb[-1:], iters - T, axis=0)])
+            gext = np.concatenate([gb, np.repeat(gb[-1:], iters - T, axis=0)])
+            e, margin, K, cv = (mu64 < 0).astype(np.uint8), float(np.abs(mu64).min()), iters, 0
+            for t in range(iters + 1):
+                if t > 0:
+                    _, post = oracle.wms_forward(Ht, st, mu64, wext[:t], gext[:t])
+                    e, margin = (post < 0).astype(np.uint8), min(margin, float(np.abs(post).min()))
+                if np.array_equal(H.astype(np.int64) @ e % 2, s[shot]):
+                    K, cv = t, 1
+                    break
+            if margin < 3e-4:
+                continue
+            compared += 1
+            assert (int(conv[shot, b]), int(its[shot, b])) == (cv, K), (shot, b)
+            bits = (cand[shot, b][np.arange(n) >> 5] >> (np.arange(n) & 31)) & 1
+            assert np.array_equal(bits.astype(np.uint8), e), (shot, b)
+    assert compared >= 0.9 * shots * R, compared
 
 
 def test_wms_forward_matches_fp64_oracle():
