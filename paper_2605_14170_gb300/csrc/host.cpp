@@ -209,10 +209,13 @@ SmallLayout small_layout(const Tanner& g, const std::vector<int>& src, int n, in
         L.sigma[r] = r;
         for (int j = 0; j < 6; ++j) L.slot[r][j] = j;
     }
+    // variables by descending degree: the last step, the one that n leaves
+    // partly empty, then holds the smallest degrees (every step costs its
+    // largest degree for all 32 lanes)
     L.order.resize(n);
     for (int v = 0; v < n; ++v) L.order[v] = v;
     std::stable_sort(L.order.begin(), L.order.end(),
-                     [&](int a, int b) { return ve[a].size() < ve[b].size(); });
+                     [&](int a, int b) { return ve[a].size() > ve[b].size(); });
     std::vector<int> posof(n);
     for (int p = 0; p < n; ++p) posof[L.order[p]] = p;
     const int steps = (n + 31) / 32;
