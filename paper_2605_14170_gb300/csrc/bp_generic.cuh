@@ -349,25 +349,30 @@ __device__ __forceinline__ void run_item(const DevBases& B, const ShotIO& io, in
 
     int K = 0;
     bool conv = false;
+    int kf = 0;  // the row group whose test failed last (group-uniform)
     for (int it = 0;; ++it) {
-        // halting rule: H e = s on the rows of H (the extra rows are copies);
-        // the first row group decides most unconverged iterations, so the
-        // other groups are tested only if it passed
+        // halting rule: H e = s on the rows of H (the extra rows are copies).
+        // One row group at a time until one fails, starting with the group
+        // that failed at the previous test: near convergence the same few
+        // checks stay unsatisfied, so one group usually decides
         bool ok = true;
-        for (int k = 0; k < orow_steps; ++k) {
+        for (int s = 0; s < orow_steps; ++s) {
+            const int k = (kf + s < orow_steps) ? kf + s : kf + s - orow_steps;
             const int r = lane + GT * k;
+            bool gok = true;
             if (r < m) {
                 uint32_t par = (sb >> k) & 1u;
 #pragma unroll
                 for (int j = 0; j < DC; ++j) par ^= eh[hcol[j * mpad + r]];
-                ok = ok && (par == 0u);
+                gok = (par == 0u);
             }
-            if (k == 0 && orow_steps > 1) {  // group-uniform condition
-                const bool first_ok = gall<G>(ok, bar);
-                if (!first_ok) break;
+            if (!gall<G>(gok, bar)) {  // group-uniform
+                ok = false;
+                kf = k;
+                break;
             }
         }
-        if (gall<G>(ok, bar)) {
+        if (ok) {
             conv = true;
             K = it;
             break;
