@@ -47,6 +47,45 @@ __host__ __device__ inline WmsLayout wms_layout(int DC, int MP, int n, int ckpt)
     return L;
 }
 
+// One variable of degree D from a packed width-6 descriptor: q_i = mu + the
+// other messages in ascending row order, as prefix sums P_i = mu + m_0 + ...
+// + m_{i-1} and q_i = P_i + m_{i+1} + ... (term for term the same sums);
+// returns the posterior P_D.  m and q share the slot layout.
+template <int D>
+__device__ __forceinline__ float wms_var_packed(const float* m, float* q, const uint4& d, float mu) {
+    uint32_t s[D];
+    float mv[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        s[i] = generic_bp::packed_off(d, i);
+        mv[i] = generic_bp::msg_at(const_cast<float*>(m), s[i]);
+    }
+    float P[D + 1];
+    P[0] = mu;
+#pragma unroll
+    for (int i = 0; i < D; ++i) P[i + 1] = __fadd_rn(P[i], mv[i]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float x = P[i];
+#pragma unroll
+        for (int k = i + 1; k < D; ++k) x = __fadd_rn(x, mv[k]);
+        generic_bp::msg_at(q, s[i]) = x;
+    }
+    return P[D];
+}
+
+__device__ __forceinline__ float wms_var_dispatch(int deg, const float* m, float* q, const uint4& d, float mu) {
+    switch (deg) {
+        case 1: return wms_var_packed<1>(m, q, d, mu);
+        case 2: return wms_var_packed<2>(m, q, d, mu);
+        case 3: return wms_var_packed<3>(m, q, d, mu);
+        case 4: return wms_var_packed<4>(m, q, d, mu);
+        case 5: return wms_var_packed<5>(m, q, d, mu);
+        case 6: return wms_var_packed<6>(m, q, d, mu);
+        default: return mu;
+    }
+}
+
 // q^(t)_e and the posterior from m (variable pass, ascending row order).
 // Each step's descriptor is loaded one step ahead; a variable's slots and
 // messages are read once into registers (at most DV of them).  G warps
@@ -60,37 +99,16 @@ __device__ __forceinline__ void wms_var_pass(const DevBases& B, int b, const uin
     const int n = B.n;
     if constexpr (DV == 6) {
         // width 6: the slots come packed in the descriptor (vdesc6), no
-        // slot-list load; byte offsets index m and q alike (same layout)
+        // slot-list load; the body is chosen by the variable's degree (the
+        // degree-sorted order keeps a warp's lanes on one case)
         const uint4* vd6 = B.vdesc6 + (size_t)b * n;
         uint4 dn = (lane < n) ? __ldg(vd6 + lane) : make_uint4(0u, 0u, 0u, 0u);
         for (int p = lane; p < n; p += GT) {
             const uint4 d = dn;
             if (p + GT < n) dn = __ldg(vd6 + p + GT);
             const int v = d.x & 0xffff, deg = (int)(d.x >> 16);
-            uint32_t s[6];
-            float mv[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                s[i] = (i < deg) ? generic_bp::packed_off(d, i) : 0u;
-                mv[i] = (i < deg) ? generic_bp::msg_at(const_cast<float*>(m), s[i]) : 0.0f;
-            }
-            // P[i] = mu + m_0 + ... + m_{i-1}; q_i = P[i] + m_{i+1} + ... (the
-            // ascending sum without m_i, term for term)
-            float P[7];
-            P[0] = mu[v];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) P[i + 1] = (i < deg) ? __fadd_rn(P[i], mv[i]) : P[i];
-            if (post) post[v] = P[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                if (i < deg) {
-                    float x = P[i];
-#pragma unroll
-                    for (int k = i + 1; k < 6; ++k)
-                        if (k < deg) x = __fadd_rn(x, mv[k]);
-                    generic_bp::msg_at(q, s[i]) = x;
-                }
-            }
+            const float pv = wms_var_dispatch(deg, m, q, d, mu[v]);
+            if (post) post[v] = pv;
         }
         return;
     }
