@@ -99,27 +99,30 @@ __device__ __forceinline__ void load_shot(const DevBases& B, const ShotIO& io, i
 }
 
 // Halting rule of the shot in slot sh: H e = s on the rows of H (the extra
-// rows of H^(t) are copies), the first row group first.  Warp-uniform result.
+// rows of H^(t) are copies), one row group at a time until one fails,
+// starting with kf, the group that failed at the slot's previous test (kf is
+// updated).  Warp-uniform result.
 template <int DC>
 __device__ __forceinline__ bool halted(int m, int mpad, const uint16_t* hcol, const uint8_t* e,
-                                       const uint32_t* sb) {
+                                       const uint32_t* sb, int& kf) {
     const int lane = threadIdx.x & 31;
-    bool ok = true;
-    for (int r0 = 0; r0 < m; r0 += 32) {
-        const int r = r0 + lane;
+    const int groups = (m + 31) >> 5;
+    for (int s = 0; s < groups; ++s) {
+        const int g = (kf + s < groups) ? kf + s : kf + s - groups;
+        const int r = 32 * g + lane;
+        bool ok = true;
         if (r < m) {
-            uint32_t par = (sb[r >> 5] >> (r & 31)) & 1u;
+            uint32_t par = (sb[g] >> lane) & 1u;
 #pragma unroll
             for (int j = 0; j < DC; ++j) par ^= e[hcol[j * mpad + r]];
-            ok = ok && (par == 0u);
+            ok = (par == 0u);
         }
-        // the first row group decides most unconverged iterations
-        if (r0 == 0 && m > 32) {  // warp-uniform condition
-            const bool first_ok = __all_sync(kFull, ok);
-            if (!first_ok) return false;
+        if (!__all_sync(kFull, ok)) {  // warp-uniform
+            kf = g;
+            return false;
         }
     }
-    return __all_sync(kFull, ok);
+    return true;
 }
 
 // Next shot of representation b from its shared counter (warp-uniform; -1
@@ -156,11 +159,12 @@ __device__ __forceinline__ void run_rep(const DevBases& B, const ShotIO& io, int
     const uint4* vd = B.vdesc3 + (size_t)b * n;
 
     // warp-uniform slot state
-    int shot[CS], iter[CS];
+    int shot[CS], iter[CS], kf[CS];
     uint32_t active = 0;
 #pragma unroll
     for (int sh = 0; sh < CS; ++sh) {
         iter[sh] = 0;
+        kf[sh] = 0;
         shot[sh] = pull_shot(ctr, io.batch);
         if (shot[sh] >= 0) {
             active |= 1u << sh;
@@ -172,13 +176,14 @@ __device__ __forceinline__ void run_rep(const DevBases& B, const ShotIO& io, int
 #pragma unroll
         for (int sh = 0; sh < CS; ++sh) {
             while ((active >> sh) & 1u) {
-                const bool ok = halted<DC>(m, mpad, hcol, eh + sh * L.EP, sbits + CS * L.RW + sh * L.RW);
+                const bool ok = halted<DC>(m, mpad, hcol, eh + sh * L.EP, sbits + CS * L.RW + sh * L.RW, kf[sh]);
                 if (!ok && iter[sh] < io.iters) break;
                 const unsigned long long item = (unsigned long long)shot[sh] * R + b;
                 generic_bp::store_item(io, item, n, W, eh + sh * L.EP, ok, iter[sh]);
                 shot[sh] = pull_shot(ctr, io.batch);
                 if (shot[sh] >= 0) {
                     iter[sh] = 0;
+                    kf[sh] = 0;
                     load_shot<DC, CS>(B, io, b, shot[sh], sh, L, msg, mu, eh, sbits);
                 } else {
                     active &= ~(1u << sh);
