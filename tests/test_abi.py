@@ -126,3 +126,13 @@ def test_random_sets_host_equals_oracle(lib):
         assert [x.tolist() for x in a] == [x.tolist() for x in b]
     with pytest.raises(lib.MBBPError):
         lib.mbbp_random_sets(10, [-1], 1)
+
+
+def test_workspace_size_queries_reject_bad_arguments(lib):
+    """Every size query answers 0 for a NULL handle (and the WMS ones for a
+    negative batch or T < 1) before touching a device."""
+    L = lib._lib
+    assert L.mbbp_decode_workspace_size(None, 10) == 0
+    assert L.mbbp_wms_workspace_size(None, 10, 25, 5) == 0
+    assert L.mbbp_wms_decode_workspace_size(None, 10, 25) == 0
+    assert L.mbbp_plan_workspace_size(None, np.zeros(1, np.int32)) == 0
