@@ -6,7 +6,8 @@
   the FP64 oracle's posteriors;
 * forward posteriors within 1e-4 relative of the FP64 oracle;
 * the hand-written adjoint (mbbp_wms_backward) within 1e-3 relative of the
-  oracle's FP64 adjoint and of FP64 central finite differences;
+  oracle's FP64 adjoint and of FP64 central finite differences, on a regular
+  and an irregular code;
 * the checkpoint interval does not change the gradients;
 * the torch.autograd.Function returns the kernel's gradients;
 * the Adam step matches its definition.
@@ -23,8 +24,7 @@ pytestmark = pytest.mark.gpu
 def _setup(code="bb72", R=2, shots=12, T=8, seed=1, p=0.07):
     import torch
     from paper_2605_14170_gb300 import mbbp
-    c = named_code(code)
-    H = c.HZ
+    H = _irregular_H(11) if code == "irregular" else named_code(code).HZ
     n = H.shape[1]
     ex, _ = oracle.sample(seed, 0, shots, n, p, "depolarizing")
     s = oracle.syndrome(H, ex)
@@ -239,6 +239,42 @@ def test_wms_gradients_match_oracle_adjoint_and_finite_differences(all_iters):
             assert abs(got[b, tt, k] - fd) <= 1e-3 * abs(fd) + 1e-9, (which, b, tt, k, got[b, tt, k], fd)
             checked += 1
     assert checked >= 16
+
+
+def test_wms_gradients_on_irregular_code_match_oracle_adjoint():
+    """Rows of weight 3 to 6: the kernels' per-row degrees, the parameters and
+    gradient sums in the message layout (zeros past a row's degree) and
+    their return to edge order, against the FP64 oracle adjoint."""
+    import torch
+    from paper_2605_14170_gb300 import mbbp
+    shots, T, ckpt = 10, 6, 2
+    H, B, s, ex, mu, w, g, t = _setup(code="irregular", R=4, shots=shots, T=T, seed=9)
+    n = H.shape[1]
+    scale = 1.0 / (shots * B.R * n)
+    w32, g32, mu32 = (x.astype(np.float32).astype(np.float64) for x in (w, g, mu))
+    gw_ref, gg_ref = np.zeros_like(w32), np.zeros_like(g32)
+    for shot in range(shots):
+        for b in range(B.R):
+            Ht, st, wb, gb, Eb = _oracle_item(H, B, s, mu32, w32, g32, ex, shot, b, scale)
+            _, gwb, ggb = oracle.wms_backward(Ht, st, mu32, wb, gb, ex[shot], scale, all_iters=True)
+            gw_ref[b][:, :Eb] += gwb
+            gg_ref[b][:, :Eb] += ggb
+    post = torch.empty((shots, B.R, n), dtype=torch.float32, device="cuda")
+    ws = torch.empty(mbbp.mbbp_wms_workspace_size(B, shots, T, ckpt), dtype=torch.uint8, device="cuda")
+    mbbp.mbbp_wms_forward(B, t["s"], t["mu"], T, t["w"], t["g"], ckpt, t["e"], scale, post, None, ws,
+                          all_iters=True)
+    gw = torch.zeros_like(t["w"])
+    gg = torch.zeros_like(t["g"])
+    mbbp.mbbp_wms_backward(B, t["s"], t["mu"], T, t["w"], t["g"], ckpt, t["e"], scale, post, gw, gg, ws,
+                           all_iters=True)
+    torch.cuda.synchronize()
+    gw, gg = gw.cpu().numpy().astype(np.float64), gg.cpu().numpy().astype(np.float64)
+    for got, ref in ((gw, gw_ref), (gg, gg_ref)):
+        assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
+        big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+        assert (np.abs(got - ref)[big] <= 1e-3 * np.abs(ref)[big] + 1e-7).mean() >= 0.99
+    for b in range(B.R):  # entries past a representation's edges stay untouched
+        assert not gw[b][:, int(B.edges[b]):].any() and not gg[b][:, int(B.edges[b]):].any()
 
 
 def test_checkpoint_interval_does_not_change_gradients():
