@@ -212,21 +212,28 @@ __device__ __forceinline__ void run_chunk(const DevBases& B, const ShotIO& io, i
         }
     }
 
-    for (int shot = shot_begin; shot < shot_end; ++shot) {
-        const unsigned long long item = (unsigned long long)shot * R + b;
-        const float* llr = io.llr + (size_t)shot * io.llr_stride;
-        const uint8_t* sy = io.synd + (size_t)shot * m;
-        float* tr = (OUT && io.c2v) ? io.c2v + item * (unsigned long long)io.c2v_stride : nullptr;
-        float mu[VS];
-        uint32_t ew[VS];
+    // channel LLRs of this lane's variables: once per chunk when every shot
+    // shares one LLR vector (llr_stride 0), else per shot
+    float mu[VS];
+    auto load_mu = [&](const float* llr) {
 #pragma unroll
         for (int k = 0; k < VS; ++k) {
             const bool live = (32 * k + lane) < n;
             const uint32_t v = __ldg(&vd[32 * k + lane].x) & 0xffffu;
             // + 0.0f turns -0 into +0: decision-neutral, keeps -0 out of every sum
             mu[k] = live ? __fadd_rn(__ldg(llr + v), 0.0f) : 0.0f;
-            ew[k] = __ballot_sync(kFull, mu[k] < 0.f);
         }
+    };
+    if (io.llr_stride == 0) load_mu(io.llr);
+
+    for (int shot = shot_begin; shot < shot_end; ++shot) {
+        const unsigned long long item = (unsigned long long)shot * R + b;
+        const uint8_t* sy = io.synd + (size_t)shot * m;
+        float* tr = (OUT && io.c2v) ? io.c2v + item * (unsigned long long)io.c2v_stride : nullptr;
+        if (io.llr_stride != 0) load_mu(io.llr + (size_t)shot * io.llr_stride);
+        uint32_t ew[VS];
+#pragma unroll
+        for (int k = 0; k < VS; ++k) ew[k] = __ballot_sync(kFull, mu[k] < 0.f);
         uint32_t sb = 0, sbo = 0;
 #pragma unroll
         for (int k = 0; k < RS; ++k)
