@@ -53,9 +53,9 @@ ALU_LANES, FMA_LANES, ISSUE_LANES = 64, 128, 128
 EDGE_UPDATES_PER_CLK_SM = min(ALU_LANES / ALU_OPS, FMA_LANES / FMA_OPS, ISSUE_LANES / OPS_PER_EDGE_UPDATE)
 # DRAM bytes per shot of the BP kernel: one ncu capture of a 100k-shot launch
 # of the current kernel and layout (profiles/decode_small_kernel_bb144_r16.md:
-# 7.311 MB read + 4.4 KB written); set to None whenever the kernel changes
+# 7.306 MB read + 2.6 KB written); set to None whenever the kernel changes
 # until it is captured again
-DRAM_BYTES_PER_SHOT = (7.310848e6 + 4.352e3) / 100000
+DRAM_BYTES_PER_SHOT = (7.305728e6 + 2.56e3) / 100000
 WORKLOAD = "[[144,12,12]] BB, depolarizing p in {0.02,0.04,0.06,0.08}, X and Z decoded, R=16, 100 iters"
 
 
