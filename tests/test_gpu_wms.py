@@ -92,7 +92,7 @@ def _irregular_H(seed, m=30, n=60):
     return H
 
 
-@pytest.mark.parametrize("code,R,shots", [("bb72", 4, 16), ("irregular", 4, 16), ("gb882", 64, 3)])
+@pytest.mark.parametrize("code,R,shots", [("bb72", 4, 16), ("irregular", 4, 16), ("bb288", 8, 6), ("gb882", 64, 3)])
 def test_wms_decode_with_learned_weights_matches_oracle(code, R, shots):
     """mbbp_wms_decode with a different weight and damping on every edge and
     iteration (T = 6, 10 iterations: the last four reuse the weights of
@@ -101,7 +101,9 @@ def test_wms_decode_with_learned_weights_matches_oracle(code, R, shots):
     halting iteration, the flag and the candidate.  Items whose posteriors
     come within 3e-4 of 0 (where FP32 rounding may decide differently; the
     forward test bounds the FP32 posteriors' error by 1e-4) are not
-    compared: a few percent of them on the length-882 code."""
+    compared: a few percent of them on the length-882 code.  The codes'
+    message areas lead the launcher to different numbers of warps per item
+    (one on [[72]], four on the length-882 code)."""
     import torch
     from paper_2605_14170_gb300 import mbbp
     T, iters = 6, 10
