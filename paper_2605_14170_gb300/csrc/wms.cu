@@ -9,11 +9,14 @@
 // Loss of an item: scale * sum_v BCE(sigmoid(-post_v), e_v), post = mu + sum m^(T),
 // or (all_iters) the mean of that over the posteriors of iterations 1..T.
 //
-// Kernels (one warp per (shot, representation), generic slot layout):
+// Kernels (generic slot layout; the backward pass one warp per (shot,
+// representation), the forward pass G warps per item, G in {1, 2, 4}):
 //   wms_forward   T iterations, posterior, loss, a checkpoint of m every
 //                 `ckpt` iterations; or, in decode mode, the halting rule
 //                 after every iteration and the candidate for FWS
-//                 (iterations past T reuse the weights of iteration T);
+//                 (iterations past T reuse the weights of iteration T),
+//                 with w and g rearranged by wms_pack beforehand into the
+//                 message layout;
 //   wms_backward  segment by segment from the last checkpoint: recompute the
 //                 segment's forward states, then the adjoint through it
 //                 (the min's derivative goes to the arg-min edge, lowest index
