@@ -388,8 +388,12 @@ __global__ void __launch_bounds__(kWmsWarps * 32, 3) wms_forward_kernel(const Wm
 
 // SMEM_ST: the segment's recomputed states sit in shared memory after the
 // warp's other arrays (small codes); otherwise in the warp's global buffer.
+// Register bound: with the states in shared memory, shared memory limits
+// the resident warps (12 per SM on [[144]]), so the kernel may take up to
+// 128 registers (measured 4.76 -> 4.69 ms on [[144]] R = 8); the global-state
+// path keeps 64 (its residency is set by registers).
 template <int DC, int DV, bool SMEM_ST>
-__global__ void __launch_bounds__(kWmsWarps * 32, 4)
+__global__ void __launch_bounds__(kWmsWarps * 32, SMEM_ST ? 2 : 4)
 wms_backward_kernel(const WmsArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevBases& B = a.B;
